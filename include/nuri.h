@@ -1,0 +1,211 @@
+/*
+ * nuri.h -- C ABI of libnuri, a single-GPU (sm_103a) implementation of prioritized subgraph
+ * expansion with pruning for exact top-k subgraph discovery (arXiv 1807.08888, "Nuri").
+ *
+ * The problem (Section 2, "Top-k Semantics"): given a data graph, a result-set size k and a
+ * ranking criterion, return the k most relevant subgraphs without enumerating all of them.
+ * Three query kinds are built in, each with the user functions the paper gives for it:
+ *   - cliques ranked by size                     (Section 3.2 example, Section 4.1, Listing 1)
+ *   - labelled subgraph isomorphism, ranked by the sum of vertex scores
+ *                                                (Section 4.3, Listing 3, Fig. 6)
+ *   - frequent labelled patterns, ranked by minimum image-based support
+ *                                                (Section 2, Section 3.3, Section 4.2, Listing 2)
+ *
+ * Conventions for every entry point:
+ *   - Every function returns a nuri_status; NURI_OK == 0.  On failure a thread-local message
+ *     is available from nuri_last_error().  Errors never abort the process and leave the
+ *     graph usable.
+ *   - Host pointers unless a flag says otherwise.  Inputs are copied; the caller keeps
+ *     ownership of everything it passes in.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Every
+ *     blocking call enqueues its work on that stream and synchronises it before returning.
+ *   - Calls on one nuri_graph are serialised by the caller (one query at a time per graph);
+ *     nuri_topk_batch runs many queries in one call.
+ *   - Results (nuri_result) are owned by the library and released with nuri_free_result.
+ *
+ * Ranking and tie-breaking (identical to the CPU oracle): rows are sorted by score descending;
+ * equal scores are ordered by the ascending sorted vertex-id list (lexicographic), then, for
+ * isomorphism matches, by the ascending sorted edge list, and, for patterns, by the canonical
+ * code.  Exactly min(k, number of relevant subgraphs) rows are returned.
+ */
+#ifndef NURI_H_
+#define NURI_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t nuri_status;
+#define NURI_OK 0
+#define NURI_ERR_INVALID 1   /* bad argument: k < 1, id out of range, bad query, ...      */
+#define NURI_ERR_OOM 2       /* device or pinned-host allocation failed                    */
+#define NURI_ERR_LIMIT 3     /* a built-in size limit was exceeded (clique size > 128, ...) */
+#define NURI_ERR_TIMEOUT 4   /* a bounded device wait ran out                              */
+#define NURI_ERR_CANCELLED 5 /* the request was cancelled                                  */
+#define NURI_ERR_CUDA 6      /* a CUDA runtime call failed                                 */
+
+/* ranking functions */
+#define NURI_RANK_SIZE 0        /* cliques: |V_s|                                           */
+#define NURI_RANK_WEIGHT_SUM 1  /* isomorphism: sum of the int32 vertex weights            */
+#define NURI_RANK_DEGREE_SUM 2  /* isomorphism: sum of vertex degrees (the paper's Sec. 6.4) */
+#define NURI_RANK_MNI 3         /* patterns: minimum image-based support                   */
+
+/* nuri_load_graph flags */
+#define NURI_LOAD_DEVICE_INPUT 0x1u /* src/dst/labels/weights are device pointers          */
+#define NURI_LOAD_NO_ISO 0x2u       /* skip label segments and hop index (cliques only)    */
+
+/* nuri_topk_cliques flags */
+#define NURI_CLIQUE_ALL 0x0u        /* every clique is relevant (the paper's relevant()=true) */
+#define NURI_CLIQUE_MAXIMAL 0x1u    /* only maximal cliques are relevant                      */
+/* flags common to all queries */
+#define NURI_KEEP_TIES 0x100u       /* return every row tied with the k-th (|R| may exceed k) */
+#define NURI_NO_PRUNE 0x200u        /* disable pruning and prioritization (Nuri-NP ablation)  */
+
+typedef struct nuri_graph nuri_graph;
+
+/* Counters of one query.  "expansions" counts child subgraphs created (Algorithm 1 line 14;
+ * for patterns, extension candidates examined), including children pruned at once. */
+typedef struct nuri_stats {
+  int64_t expansions;      /* children created                                   */
+  int64_t pruned;          /* children or records dropped by the bound            */
+  int64_t dequeued;        /* frontier records / seeds processed                  */
+  int64_t spilled;         /* frontier records copied to pinned host memory       */
+  int64_t reloaded;        /* spilled records copied back                         */
+  int64_t results_stored;  /* candidate results written to the device result set  */
+  int64_t rounds;          /* frontier rounds (kernel launches of the expansion)  */
+  int64_t adj_bytes;       /* algorithmic bytes of adjacency read by expansions   */
+  int64_t threshold;       /* final k-th best score (INT64_MIN if < k results)    */
+  int32_t restarts;        /* result-set overflows that forced a re-run          */
+  int32_t pad;
+  double device_ms;        /* device time from first to last kernel of the query  */
+  int64_t launches;        /* kernels of this library launched by the query       */
+  int64_t expand_launches; /* launches of the expansion kernel                    */
+  double expand_ms;        /* summed device time of those launches (CUDA events)  */
+} nuri_stats;
+
+/* A result set.  Row i has score[i]; its vertices are verts[vert_off[i] .. vert_off[i+1])
+ * (ascending original ids for cliques and isomorphism matches; canonical pattern vertex
+ * indices 0..nv-1 for patterns, with labels[] holding each vertex's label); its edges are
+ * the pairs edges[2*j], edges[2*j+1] for j in [edge_off[i], edge_off[i+1]) (isomorphism:
+ * (min,max) original ids sorted ascending; patterns: canonical index pairs; cliques: none). */
+typedef struct nuri_result {
+  int32_t count;
+  int32_t kind;       /* 0 cliques, 1 isomorphism, 2 patterns */
+  int64_t* score;
+  int32_t* vert_off;
+  int32_t* verts;
+  int32_t* edge_off;
+  int32_t* edges;
+  int32_t* labels;    /* patterns only (NULL otherwise) */
+  nuri_stats stats;
+} nuri_result;
+
+/* A connected query graph for subgraph isomorphism: nq <= 8 vertices with labels, ne edges
+ * given as pairs (src[e], dst[e]) of query vertex indices (host memory). */
+typedef struct nuri_query {
+  int32_t nq;
+  int32_t ne;
+  const uint8_t* labels;
+  const int32_t* src;
+  const int32_t* dst;
+} nuri_query;
+
+/* Static facts about a loaded graph. */
+typedef struct nuri_graph_info {
+  int32_t n;
+  int32_t num_labels;    /* 0 when the graph has no labels */
+  int64_t num_edges;     /* undirected edges after clean-up */
+  int64_t dropped;       /* input pairs dropped (self-loops and duplicates) */
+  int32_t max_degree;
+  int32_t max_out_degree;/* in the degree orientation used for cliques */
+  int32_t index_hops;    /* hops of the hop/label index that is resident */
+  int32_t pad;
+  int64_t device_bytes;  /* device memory held by the graph */
+} nuri_graph_info;
+
+/*
+ * nuri_load_graph -- build the device-resident graph (Section 5: the engine loads the data
+ * graph into memory; Section 4.3: initialize() builds the per-vertex index at load time).
+ *   n          number of vertices, ids 0..n-1 (0 <= n < 2^31)
+ *   m          number of input pairs; src[e], dst[e] in [0, n).  Undirected: either or both
+ *              directions may be given; self-loops and duplicates are dropped.
+ *   labels     uint8 per vertex, or NULL (then isomorphism/pattern queries are rejected)
+ *   weights    int32 per vertex (>= 0), or NULL (weight-sum ranking then rejected)
+ *   index_hops hops H of the hop/label max index to build (0 = none; <= 7).  Queries whose
+ *              radius exceeds H fall back to a per-label global maximum for the far vertices.
+ *   flags      NURI_LOAD_*
+ *   out        receives the graph handle (free with nuri_free_graph)
+ * Errors: NURI_ERR_INVALID (bad sizes or ids), NURI_ERR_OOM, NURI_ERR_CUDA.
+ */
+nuri_status nuri_load_graph(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                            const uint8_t* labels, const int32_t* weights, int32_t index_hops,
+                            uint32_t flags, void* stream, nuri_graph** out);
+void nuri_free_graph(nuri_graph* g);
+nuri_status nuri_graph_get_info(const nuri_graph* g, nuri_graph_info* info);
+
+/*
+ * nuri_topk_cliques -- top-k cliques by size (Algorithm 1 with the clique functions of
+ * Section 3.2: candidate set P_s of Listing 1 restricted by canonical extension, bound
+ * |V_s| + |P_s| (Carraghan-Pardalos), prune a subgraph iff its bound < the k-th best size).
+ *   k      >= 1
+ *   rank   NURI_RANK_SIZE
+ *   flags  NURI_CLIQUE_ALL (default: every clique, singletons included, is a result) or
+ *          NURI_CLIQUE_MAXIMAL; optionally NURI_KEEP_TIES, NURI_NO_PRUNE
+ *   frontier_cap  maximum number of frontier records kept on the device before the lowest
+ *          buckets are spilled to pinned host memory (0 = library default)
+ * Errors: NURI_ERR_INVALID, NURI_ERR_LIMIT (a clique larger than 128), NURI_ERR_OOM, CUDA.
+ */
+nuri_status nuri_topk_cliques(nuri_graph* g, int32_t k, int32_t rank, uint32_t flags,
+                              int64_t frontier_cap, void* stream, nuri_result** out);
+
+/*
+ * nuri_topk_iso -- top-k subgraphs isomorphic to a query (Section 2 definition, non-induced
+ * image subgraphs; Section 4.3 functions: score = sum of vertex scores, upper bound =
+ * score + sum over unmatched query vertices of index(root image, label, hop)).
+ *   rank   NURI_RANK_WEIGHT_SUM or NURI_RANK_DEGREE_SUM
+ * Errors: NURI_ERR_INVALID (nq outside 1..8, disconnected query, no labels/weights).
+ */
+nuri_status nuri_topk_iso(nuri_graph* g, const nuri_query* q, int32_t k, int32_t rank,
+                          uint32_t flags, void* stream, nuri_result** out);
+
+/*
+ * nuri_topk_iso_batch -- nq_batch isomorphism queries in one call; the seeds and frontiers of
+ * all queries are expanded together by the same kernels.  outs[i] receives query i's result.
+ */
+nuri_status nuri_topk_iso_batch(nuri_graph* g, int32_t nqueries, const nuri_query* qs,
+                                const int32_t* ks, int32_t rank, uint32_t flags, void* stream,
+                                nuri_result** outs);
+
+/*
+ * nuri_topk_patterns -- top-k connected vertex-labelled patterns with exactly M edges by
+ * minimum image-based support (Algorithm 2, Section 4.2 functions: priority (m, f),
+ * dominated = f < f(k-th)).  1 <= M <= 5.
+ */
+nuri_status nuri_topk_patterns(nuri_graph* g, int32_t M, int32_t k, int32_t rank,
+                               uint32_t flags, void* stream, nuri_result** out);
+
+/*
+ * nuri_hop_index -- copy the resident hop/label index to the caller: out[((h-1)*n+v)*L+l]
+ * = max weight (or degree if degree_rank) over vertices of label l reachable from v by a walk
+ * of 1..h edges, -1 when there is none (Section 4.3, Listing 3; cumulative-hop reading).
+ * `out` is a device pointer when `device_out` is non-zero, else host.  hops <= index_hops.
+ */
+nuri_status nuri_hop_index(nuri_graph* g, int32_t hops, int32_t degree_rank, int32_t* out,
+                           int32_t device_out, void* stream);
+
+void nuri_free_result(nuri_result* r);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char* nuri_last_error(void);
+
+/* Library version string. */
+const char* nuri_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NURI_H_ */

@@ -1,0 +1,297 @@
+"""Python binding of libnuri (C ABI in include/nuri.h): argument marshalling only.
+
+Every step of a query runs inside libnuri's CUDA kernels; this module converts arrays to
+pointers, calls the C entry points and turns the library-owned result into Python rows.
+There is no CPU fallback: if ``libnuri.so`` is missing or fails to load, every call raises.
+
+    import paper_1807_08888_b300 as nuri
+    g = nuri.load_graph(n, src, dst, labels=None, weights=None, index_hops=0)
+    rows = nuri.topk_cliques(g, k=10)             # [(size, (ids...)), ...]
+    rows = nuri.topk_iso(g, query, k=1000)        # [(score, (ids...), ((a,b),...)), ...]
+    rows = nuri.topk_patterns(g, M=3, k=10)       # [(support, (labels...), ((i,j),...)), ...]
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+__all__ = [
+    "NuriError", "lib", "load_graph", "Graph", "topk_cliques", "topk_iso", "topk_iso_batch",
+    "topk_patterns", "hop_index", "Result", "LIB_PATH", "EXPORTS",
+    "RANK_SIZE", "RANK_WEIGHT_SUM", "RANK_DEGREE_SUM", "RANK_MNI",
+]
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnuri.so")
+
+OK, ERR_INVALID, ERR_OOM, ERR_LIMIT, ERR_TIMEOUT, ERR_CANCELLED, ERR_CUDA = range(7)
+RANK_SIZE, RANK_WEIGHT_SUM, RANK_DEGREE_SUM, RANK_MNI = range(4)
+LOAD_DEVICE_INPUT, LOAD_NO_ISO = 0x1, 0x2
+CLIQUE_ALL, CLIQUE_MAXIMAL = 0x0, 0x1
+KEEP_TIES, NO_PRUNE = 0x100, 0x200
+
+# every function include/nuri.h declares
+EXPORTS = (
+    "nuri_load_graph", "nuri_free_graph", "nuri_graph_get_info", "nuri_topk_cliques",
+    "nuri_topk_iso", "nuri_topk_iso_batch", "nuri_topk_patterns", "nuri_hop_index",
+    "nuri_free_result", "nuri_last_error", "nuri_version",
+)
+
+
+class NuriError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"nuri error {code}: {msg}")
+        self.code = code
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [
+        ("expansions", ctypes.c_int64), ("pruned", ctypes.c_int64),
+        ("dequeued", ctypes.c_int64), ("spilled", ctypes.c_int64),
+        ("reloaded", ctypes.c_int64), ("results_stored", ctypes.c_int64),
+        ("rounds", ctypes.c_int64), ("adj_bytes", ctypes.c_int64),
+        ("threshold", ctypes.c_int64), ("restarts", ctypes.c_int32), ("pad", ctypes.c_int32),
+        ("device_ms", ctypes.c_double), ("launches", ctypes.c_int64),
+        ("expand_launches", ctypes.c_int64), ("expand_ms", ctypes.c_double),
+    ]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [
+        ("count", ctypes.c_int32), ("kind", ctypes.c_int32),
+        ("score", ctypes.POINTER(ctypes.c_int64)),
+        ("vert_off", ctypes.POINTER(ctypes.c_int32)), ("verts", ctypes.POINTER(ctypes.c_int32)),
+        ("edge_off", ctypes.POINTER(ctypes.c_int32)), ("edges", ctypes.POINTER(ctypes.c_int32)),
+        ("labels", ctypes.POINTER(ctypes.c_int32)),
+        ("stats", _Stats),
+    ]
+
+
+class _Query(ctypes.Structure):
+    _fields_ = [
+        ("nq", ctypes.c_int32), ("ne", ctypes.c_int32),
+        ("labels", ctypes.c_void_p), ("src", ctypes.c_void_p), ("dst", ctypes.c_void_p),
+    ]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int32), ("num_labels", ctypes.c_int32), ("num_edges", ctypes.c_int64),
+        ("dropped", ctypes.c_int64), ("max_degree", ctypes.c_int32),
+        ("max_out_degree", ctypes.c_int32), ("index_hops", ctypes.c_int32),
+        ("pad", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load libnuri.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise NuriError(ERR_CUDA, f"{LIB_PATH} is not built "
+                                          "(python -m paper_1807_08888_b300.build)")
+            L = ctypes.CDLL(LIB_PATH)
+            P, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+            RPP = ctypes.POINTER(ctypes.POINTER(_Result))
+            L.nuri_load_graph.argtypes = [i32, i64, P, P, P, P, i32, u32, P,
+                                          ctypes.POINTER(ctypes.c_void_p)]
+            L.nuri_load_graph.restype = i32
+            L.nuri_free_graph.argtypes = [P]
+            L.nuri_free_graph.restype = None
+            L.nuri_graph_get_info.argtypes = [P, ctypes.POINTER(_Info)]
+            L.nuri_graph_get_info.restype = i32
+            L.nuri_topk_cliques.argtypes = [P, i32, i32, u32, i64, P, RPP]
+            L.nuri_topk_cliques.restype = i32
+            L.nuri_topk_iso.argtypes = [P, ctypes.POINTER(_Query), i32, i32, u32, P, RPP]
+            L.nuri_topk_iso.restype = i32
+            L.nuri_topk_iso_batch.argtypes = [P, i32, ctypes.POINTER(_Query), P, i32, u32, P,
+                                              ctypes.POINTER(ctypes.POINTER(_Result))]
+            L.nuri_topk_iso_batch.restype = i32
+            L.nuri_topk_patterns.argtypes = [P, i32, i32, i32, u32, P, RPP]
+            L.nuri_topk_patterns.restype = i32
+            L.nuri_hop_index.argtypes = [P, i32, i32, P, i32, P]
+            L.nuri_hop_index.restype = i32
+            L.nuri_free_result.argtypes = [ctypes.POINTER(_Result)]
+            L.nuri_free_result.restype = None
+            L.nuri_last_error.restype = ctypes.c_char_p
+            L.nuri_version.restype = ctypes.c_char_p
+            _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != OK:
+        raise NuriError(rc, lib().nuri_last_error().decode(errors="replace"))
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return ctypes.c_void_p(0)
+
+
+def _host_ptr(a, dtype):
+    if a is None:
+        return None, None
+    arr = np.ascontiguousarray(np.asarray(a), dtype=dtype)
+    return arr, arr.ctypes.data_as(ctypes.c_void_p)
+
+
+class Result(list):
+    """Rows in rank order plus the query's device counters (``stats``, a dict)."""
+    stats: dict = {}
+
+
+def _unpack(rp) -> Result:
+    r = rp.contents
+    out = Result()
+    n = r.count
+    score = np.ctypeslib.as_array(r.score, shape=(max(n, 1),))[:n].copy() if n else np.zeros(0)
+    voff = np.ctypeslib.as_array(r.vert_off, shape=(n + 1,)).copy()
+    eoff = np.ctypeslib.as_array(r.edge_off, shape=(n + 1,)).copy()
+    nvt, net = int(voff[-1]), int(eoff[-1])
+    verts = np.ctypeslib.as_array(r.verts, shape=(max(nvt, 1),))[:nvt].copy()
+    edges = np.ctypeslib.as_array(r.edges, shape=(max(2 * net, 2),))[:2 * net].copy()
+    labels = (np.ctypeslib.as_array(r.labels, shape=(max(nvt, 1),))[:nvt].copy()
+              if r.labels else None)
+    for i in range(n):
+        v = tuple(int(x) for x in verts[voff[i]:voff[i + 1]])
+        e = tuple((int(edges[2 * j]), int(edges[2 * j + 1])) for j in range(eoff[i], eoff[i + 1]))
+        if r.kind == 0:
+            out.append((int(score[i]), v))
+        elif r.kind == 1:
+            out.append((int(score[i]), v, e))
+        else:
+            lab = tuple(int(x) for x in labels[voff[i]:voff[i + 1]])
+            out.append((int(score[i]), lab, e))
+    s = r.stats
+    out.stats = {f: getattr(s, f) for f, _ in _Stats._fields_ if f != "pad"}
+    lib().nuri_free_result(rp)
+    return out
+
+
+class Graph:
+    """A device-resident graph (owns a nuri_graph*)."""
+
+    def __init__(self, handle):
+        self._h = handle
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise NuriError(ERR_INVALID, "graph already freed")
+        return self._h
+
+    def info(self) -> dict:
+        inf = _Info()
+        _check(lib().nuri_graph_get_info(self.handle, ctypes.byref(inf)))
+        return {f: getattr(inf, f) for f, _ in _Info._fields_ if f != "pad"}
+
+    def free(self):
+        if self._h:
+            lib().nuri_free_graph(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def load_graph(n, src, dst, labels=None, weights=None, index_hops=0, flags=0,
+               stream=None) -> Graph:
+    """Build the device graph from an undirected edge list (host arrays or CUDA tensors)."""
+    keep = []
+    if hasattr(src, "is_cuda") and src.is_cuda:
+        flags |= LOAD_DEVICE_INPUT
+        ptrs = []
+        for t in (src, dst, labels, weights):
+            if t is None:
+                ptrs.append(None)
+            else:
+                t = t.contiguous()
+                keep.append(t)
+                ptrs.append(ctypes.c_void_p(t.data_ptr()))
+        ps, pd, pl, pw = ptrs
+        m = int(src.numel())
+    else:
+        s, ps = _host_ptr(src, np.int32)
+        d, pd = _host_ptr(dst, np.int32)
+        lab, pl = _host_ptr(labels, np.uint8)
+        w, pw = _host_ptr(weights, np.int32)
+        keep += [s, d, lab, w]
+        m = int(s.size)
+    h = ctypes.c_void_p()
+    _check(lib().nuri_load_graph(int(n), m, ps, pd, pl, pw, int(index_hops), int(flags),
+                                 _stream(stream), ctypes.byref(h)))
+    return Graph(h)
+
+
+def topk_cliques(g: Graph, k: int, maximal=False, keep_ties=False, no_prune=False,
+                 frontier_cap=0, stream=None) -> Result:
+    flags = (CLIQUE_MAXIMAL if maximal else CLIQUE_ALL) | (KEEP_TIES if keep_ties else 0) | \
+        (NO_PRUNE if no_prune else 0)
+    rp = ctypes.POINTER(_Result)()
+    _check(lib().nuri_topk_cliques(g.handle, int(k), RANK_SIZE, flags, int(frontier_cap),
+                                   _stream(stream), ctypes.byref(rp)))
+    return _unpack(rp)
+
+
+def _query_struct(q, keep):
+    lab = np.ascontiguousarray(q.labels, dtype=np.uint8)
+    e = np.asarray(q.edges, dtype=np.int32).reshape(-1, 2)
+    s, d = np.ascontiguousarray(e[:, 0]), np.ascontiguousarray(e[:, 1])
+    keep += [lab, s, d]
+    return _Query(int(q.nq), int(s.size), lab.ctypes.data, s.ctypes.data, d.ctypes.data)
+
+
+def topk_iso(g: Graph, q, k: int, degree_rank=False, keep_ties=False, stream=None) -> Result:
+    return topk_iso_batch(g, [q], [k], degree_rank, keep_ties, stream)[0]
+
+
+def topk_iso_batch(g: Graph, queries, ks, degree_rank=False, keep_ties=False,
+                   stream=None) -> list:
+    keep = []
+    nq = len(queries)
+    arr = (_Query * nq)(*[_query_struct(q, keep) for q in queries])
+    kk = np.ascontiguousarray(ks, dtype=np.int32)
+    outs = (ctypes.POINTER(_Result) * nq)()
+    rank = RANK_DEGREE_SUM if degree_rank else RANK_WEIGHT_SUM
+    flags = KEEP_TIES if keep_ties else 0
+    _check(lib().nuri_topk_iso_batch(g.handle, nq, arr, kk.ctypes.data_as(ctypes.c_void_p),
+                                     rank, flags, _stream(stream), outs))
+    return [_unpack(outs[i]) for i in range(nq)]
+
+
+def topk_patterns(g: Graph, M: int, k: int, stream=None) -> Result:
+    rp = ctypes.POINTER(_Result)()
+    _check(lib().nuri_topk_patterns(g.handle, int(M), int(k), RANK_MNI, 0, _stream(stream),
+                                    ctypes.byref(rp)))
+    return _unpack(rp)
+
+
+def hop_index(g: Graph, hops: int, degree_rank=False, stream=None) -> np.ndarray:
+    inf = g.info()
+    out = np.empty((hops, inf["n"], max(inf["num_labels"], 1)), dtype=np.int32)
+    _check(lib().nuri_hop_index(g.handle, int(hops), int(bool(degree_rank)),
+                                out.ctypes.data_as(ctypes.c_void_p), 0, _stream(stream)))
+    return out
+
+
+def version() -> str:
+    return lib().nuri_version().decode()

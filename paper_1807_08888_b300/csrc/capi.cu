@@ -1,0 +1,193 @@
+// C ABI of libnuri (declared in include/nuri.h): argument checks, error conversion, result
+// allocation.  Every entry point catches the library's internal errors and returns a status.
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "nuri_internal.cuh"
+
+namespace nuri {
+
+static thread_local char g_err[1024] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+const char* last_error() { return g_err; }
+
+nuri_result* new_result(int kind, int32_t count, int64_t nverts, int64_t nedges, bool labels) {
+  nuri_result* r = (nuri_result*)calloc(1, sizeof(nuri_result));
+  if (!r) NURI_FAIL(NURI_ERR_OOM, "host allocation failed");
+  r->count = count;
+  r->kind = kind;
+  r->score = (int64_t*)calloc((size_t)count + 1, sizeof(int64_t));
+  r->vert_off = (int32_t*)calloc((size_t)count + 1, sizeof(int32_t));
+  r->edge_off = (int32_t*)calloc((size_t)count + 1, sizeof(int32_t));
+  r->verts = (int32_t*)calloc((size_t)nverts + 1, sizeof(int32_t));
+  r->edges = (int32_t*)calloc((size_t)(2 * nedges) + 2, sizeof(int32_t));
+  r->labels = labels ? (int32_t*)calloc((size_t)nverts + 1, sizeof(int32_t)) : nullptr;
+  if (!r->score || !r->vert_off || !r->edge_off || !r->verts || !r->edges ||
+      (labels && !r->labels)) {
+    nuri_free_result(r);
+    NURI_FAIL(NURI_ERR_OOM, "host allocation failed");
+  }
+  return r;
+}
+
+template <class F>
+static nuri_status guarded(F&& f) {
+  g_err[0] = 0;
+  try {
+    f();
+    return NURI_OK;
+  } catch (const Err& e) {
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    set_error("host allocation failed");
+    return NURI_ERR_OOM;
+  } catch (...) {
+    set_error("unexpected internal error");
+    return NURI_ERR_CUDA;
+  }
+}
+
+}  // namespace nuri
+
+using namespace nuri;
+
+extern "C" {
+
+const char* nuri_last_error(void) { return nuri::last_error(); }
+
+const char* nuri_version(void) { return "nuri-b300 0.1 (sm_103a)"; }
+
+nuri_status nuri_load_graph(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                            const uint8_t* labels, const int32_t* weights, int32_t index_hops,
+                            uint32_t flags, void* stream, nuri_graph** out) {
+  return guarded([&] {
+    if (!out) NURI_FAIL(NURI_ERR_INVALID, "nuri_load_graph: out is NULL");
+    *out = nullptr;
+    if (n < 0 || m < 0) NURI_FAIL(NURI_ERR_INVALID, "nuri_load_graph: negative size");
+    if (m > 0 && (!src || !dst)) NURI_FAIL(NURI_ERR_INVALID, "nuri_load_graph: NULL edge arrays");
+    if (index_hops < 0 || index_hops > 7)
+      NURI_FAIL(NURI_ERR_INVALID, "nuri_load_graph: index_hops must be in 0..7");
+    cudaStream_t s = (cudaStream_t)stream;
+    nuri_graph* g = new nuri_graph();
+    g->stream = s;
+    try {
+      build_graph(g, n, m, src, dst, labels, weights, index_hops, flags, s);
+    } catch (...) {
+      delete g;
+      throw;
+    }
+    *out = g;
+  });
+}
+
+void nuri_free_graph(nuri_graph* g) {
+  if (!g) return;
+  cudaStream_t s = g->stream;
+  delete g;  // DBuf destructors free stream-ordered
+  cudaStreamSynchronize(s);
+}
+
+nuri_status nuri_graph_get_info(const nuri_graph* g, nuri_graph_info* info) {
+  return guarded([&] {
+    if (!g || !info) NURI_FAIL(NURI_ERR_INVALID, "nuri_graph_get_info: NULL argument");
+    memset(info, 0, sizeof(*info));
+    info->n = g->d.n;
+    info->num_labels = g->d.L;
+    info->num_edges = g->num_edges;
+    info->dropped = g->dropped;
+    info->max_degree = g->d.max_deg;
+    info->max_out_degree = g->d.max_out;
+    info->index_hops = g->d.H;
+    info->device_bytes = g->device_bytes();
+  });
+}
+
+nuri_status nuri_topk_cliques(nuri_graph* g, int32_t k, int32_t rank, uint32_t flags,
+                              int64_t frontier_cap, void* stream, nuri_result** out) {
+  return guarded([&] {
+    if (!g || !out) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_cliques: NULL argument");
+    *out = nullptr;
+    if (k < 1) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_cliques: k must be >= 1");
+    if (rank != NURI_RANK_SIZE) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_cliques: rank must be NURI_RANK_SIZE");
+    if (frontier_cap < 0) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_cliques: negative frontier_cap");
+    topk_cliques(g, k, flags, frontier_cap, (cudaStream_t)stream, out);
+  });
+}
+
+nuri_status nuri_topk_iso(nuri_graph* g, const nuri_query* q, int32_t k, int32_t rank,
+                          uint32_t flags, void* stream, nuri_result** out) {
+  return nuri_topk_iso_batch(g, 1, q, &k, rank, flags, stream, out);
+}
+
+nuri_status nuri_topk_iso_batch(nuri_graph* g, int32_t nqueries, const nuri_query* qs,
+                                const int32_t* ks, int32_t rank, uint32_t flags, void* stream,
+                                nuri_result** outs) {
+  return guarded([&] {
+    if (!g || !qs || !ks || !outs) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_iso: NULL argument");
+    if (nqueries < 1) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_iso: no queries");
+    for (int i = 0; i < nqueries; ++i) outs[i] = nullptr;
+    if (rank != NURI_RANK_WEIGHT_SUM && rank != NURI_RANK_DEGREE_SUM)
+      NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_iso: rank must be WEIGHT_SUM or DEGREE_SUM");
+    if (!g->d.labels || !g->d.lsoff) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_iso: graph has no labels");
+    if (rank == NURI_RANK_WEIGHT_SUM && !g->d.weights)
+      NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_iso: graph has no weights");
+    for (int i = 0; i < nqueries; ++i) {
+      if (ks[i] < 1) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_iso: k must be >= 1");
+      const nuri_query& q = qs[i];
+      if (q.nq < 1 || q.nq > 8) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_iso: query size must be 1..8");
+      if (q.ne < 0 || (q.ne > 0 && (!q.src || !q.dst)) || !q.labels)
+        NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_iso: bad query arrays");
+    }
+    topk_iso_batch(g, nqueries, qs, ks, rank, flags, (cudaStream_t)stream, outs);
+  });
+}
+
+nuri_status nuri_topk_patterns(nuri_graph* g, int32_t M, int32_t k, int32_t rank,
+                               uint32_t flags, void* stream, nuri_result** out) {
+  return guarded([&] {
+    if (!g || !out) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_patterns: NULL argument");
+    *out = nullptr;
+    if (k < 1) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_patterns: k must be >= 1");
+    if (M < 1 || M > 5) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_patterns: M must be 1..5");
+    if (rank != NURI_RANK_MNI) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_patterns: rank must be NURI_RANK_MNI");
+    if (!g->d.labels || !g->d.lsoff) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_patterns: graph has no labels");
+    topk_patterns(g, M, k, flags, (cudaStream_t)stream, out);
+  });
+}
+
+void nuri_free_result(nuri_result* r) {
+  if (!r) return;
+  free(r->score);
+  free(r->vert_off);
+  free(r->verts);
+  free(r->edge_off);
+  free(r->edges);
+  free(r->labels);
+  free(r);
+}
+
+}  // extern "C"
+
+extern "C" nuri_status nuri_hop_index(nuri_graph* g, int32_t hops, int32_t degree_rank,
+                                      int32_t* out, int32_t device_out, void* stream) {
+  return guarded([&] {
+    if (!g || !out) NURI_FAIL(NURI_ERR_INVALID, "nuri_hop_index: NULL argument");
+    if (hops < 1 || hops > g->d.H) NURI_FAIL(NURI_ERR_INVALID, "nuri_hop_index: hops must be in 1..%d", g->d.H);
+    const int32_t* src = degree_rank ? g->d.idx_d : g->d.idx_w;
+    if (!src) NURI_FAIL(NURI_ERR_INVALID, "nuri_hop_index: index not built");
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t bytes = sizeof(int32_t) * (size_t)hops * g->d.n * g->d.L;
+    NURI_CUDA(cudaMemcpyAsync(out, src, bytes, device_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    NURI_CUDA(cudaStreamSynchronize(s));
+  });
+}

@@ -1,0 +1,942 @@
+// Top-k cliques by size: Algorithm 1 (Section 3.2) with the clique user functions of
+// Section 3.2 / Section 4.1 on the GPU.
+//
+//   P_s        = common neighbours of the members that come after every member in the
+//                canonical order (Listing 1's set with the canonical extension of Section 3.2);
+//                here the order is the degree orientation rank (any total order enumerates
+//                every clique exactly once; results are reported in original ids)
+//   expandable = d in P_s;  relevant = true (all cliques) or maximality (flag)
+//   bound      = |V_s| + |P_s| (Carraghan-Pardalos);  prune iff bound < tau (strict)
+//   tau        = k-th best size among results found so far (global, atomicMax, monotone)
+//
+// Work is organised as a bucketed best-first frontier driven from the host:
+//   * seeds (one per vertex, Alg.1 lines 1-3) are sorted by bound and consumed in
+//     descending-bound chunks; frontier records live in 64 buckets keyed by bound;
+//   * each round takes the highest bucket (or seed chunk) whose bound >= tau and expands it
+//     with one warp per record (k_clique_expand);
+//   * a record with |P| <= 64 is finished in place: the warp builds the 64x64 bit adjacency
+//     of P in shared memory and its lanes run independent depth-first searches over the
+//     subtrees of the record's children with AND + popc (the bitmap tail);
+//   * a record with |P| > 64 is split: for every d in P the warp intersects the suffix of P
+//     after d with N+(d) (binary search + ballot/popc), and children whose bound >= tau go
+//     to a staging array that is scattered into the buckets;
+//   * buckets that overflow the device frontier capacity are spilled to pinned host memory
+//     (the role of the paper's disk-backed virtual priority queue, Section 5) and reloaded,
+//     filtered by tau, when they become the highest bucket.
+// Results (clique records with size >= tau when processed) are appended to a device buffer;
+// a histogram of their sizes drives tau.  A final kernel sequence selects the rows with
+// size >= tau, maps them to original ids, sorts them by (size desc, ids lex asc) and keeps k.
+#include <cub/cub.cuh>
+
+#include <algorithm>
+#include <climits>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "nuri_internal.cuh"
+#include "topk_common.cuh"
+
+namespace nuri {
+namespace {
+
+constexpr int MAXD = 128;      // largest clique the records can hold
+constexpr int BM = 64;         // bitmap tail handles |P| <= BM
+constexpr int NB = 64;         // frontier buckets (bucket NB-1 holds every bound >= NB-1)
+constexpr int WARPS = 4;       // warps per CTA of the expansion kernel
+constexpr int PSMEM = 512;     // P entries staged in shared memory per warp
+
+struct Rec {
+  int32_t nv;
+  int32_t bound;
+  int32_t V[MAXD];  // ranks, ascending
+};
+
+struct QState {
+  int32_t tau;
+  int32_t err;           // bit 0: clique larger than MAXD
+  int64_t res_count;     // results appended (may exceed the capacity: then a re-run)
+  int64_t stage_count;   // children slots reserved in the staging array
+  int64_t defer_count;   // parents sent back because the staging array was full
+  int64_t work_next;     // dynamic work counter
+  unsigned long long expansions, pruned, dequeued, adj_bytes;
+  int32_t hist[MAXD + 2];
+};
+
+__device__ __forceinline__ int lower_bound_dev(const int32_t* a, int lo, int hi, int32_t x) {
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (a[mid] < x) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int64_t lower_bound_dev64(const int32_t* a, int64_t lo, int64_t hi,
+                                                     int32_t x) {
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (__ldg(a + mid) < x) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ bool contains64(const int32_t* a, int64_t lo, int64_t hi, int32_t x) {
+  int64_t p = lower_bound_dev64(a, lo, hi, x);
+  return p < hi && __ldg(a + p) == x;
+}
+
+// Is the clique C (ranks) maximal, i.e. does no vertex outside it touch every member?
+__device__ bool is_maximal(const DevGraph& g, const int32_t* C, int c) {
+  int best = 0;
+  int32_t bestdeg = INT32_MAX;
+  int32_t ids[MAXD + 1];
+  for (int i = 0; i < c; ++i) {
+    ids[i] = __ldg(g.vert_of + C[i]);
+    int32_t d = __ldg(g.deg + ids[i]);
+    if (d < bestdeg) {
+      bestdeg = d;
+      best = i;
+    }
+  }
+  int64_t b = g.off[ids[best]], e = g.off[ids[best] + 1];
+  for (int64_t t = b; t < e; ++t) {
+    int32_t w = __ldg(g.adj + t);
+    bool all = true;
+    for (int i = 0; i < c && all; ++i) {
+      if (i == best) continue;
+      if (ids[i] == w) {
+        all = false;
+        break;
+      }
+      all = contains64(g.adj, g.off[ids[i]], g.off[ids[i] + 1], w);
+    }
+    if (all) return false;
+  }
+  return true;
+}
+
+struct Ctx {
+  DevGraph g;
+  QState* st;
+  Rec* res;
+  int64_t res_cap;
+  Rec* stage;
+  int64_t stage_cap;
+  Rec* deferred;
+  int32_t* pscratch;    // per-warp global P buffer (max_out entries each)
+  int64_t pscratch_stride;
+  int32_t k;
+  int32_t maximal;
+  int32_t no_prune;
+};
+
+// Append one clique (ranks) of size c as a candidate result and refresh tau.
+__device__ void add_result(const Ctx& cx, const int32_t* V, int nv, int32_t extra_count,
+                           const int32_t* extra) {
+  int c = nv + extra_count;
+  int64_t slot = (int64_t)atomicAdd((unsigned long long*)&cx.st->res_count, 1ull);
+  if (slot < cx.res_cap) {
+    Rec* r = cx.res + slot;
+    r->nv = c;
+    r->bound = c;
+    for (int i = 0; i < nv; ++i) r->V[i] = V[i];
+    for (int i = 0; i < extra_count; ++i) r->V[nv + i] = extra[i];
+  }
+  atomicAdd(&cx.st->hist[c], 1);
+  publish_threshold(cx.st->hist, MAXD + 1, 0, cx.k, &cx.st->tau);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Expansion kernel: one warp per record (dynamic assignment).
+//   seeds != nullptr: record i is the seed vertex seeds[i] (nv = 1)
+//   otherwise       : record i is in[i]
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(WARPS * 32) k_clique_expand(Ctx cx, const Rec* __restrict__ in,
+                                                              const int32_t* __restrict__ seeds,
+                                                              int64_t nin) {
+  __shared__ int32_t sP[WARPS][PSMEM];
+  __shared__ unsigned long long sRow[WARPS][BM];
+  __shared__ int32_t sV[WARPS][MAXD];
+
+  const int lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
+  const unsigned FULL = 0xffffffffu;
+  const DevGraph& g = cx.g;
+  const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int32_t* scratch = cx.pscratch ? cx.pscratch + gwarp * cx.pscratch_stride : nullptr;
+
+  unsigned long long my_exp = 0, my_pruned = 0, my_deq = 0, my_bytes = 0;
+
+  while (true) {
+    int64_t item = 0;
+    __syncwarp();  // every lane is done with the previous record's shared state
+    if (lane == 0) item = (int64_t)atomicAdd((unsigned long long*)&cx.st->work_next, 1ull);
+    item = __shfl_sync(FULL, item, 0);
+    if (item >= nin) break;
+
+    // ---- load the record ----
+    int nv;
+    if (seeds) {
+      nv = 1;
+      if (lane == 0) sV[w][0] = seeds[item];
+    } else {
+      nv = in[item].nv;
+      for (int i = lane; i < nv; i += 32) sV[w][i] = in[item].V[i];
+    }
+    __syncwarp();
+    if (lane == 0) ++my_deq;
+
+    // ---- candidate set P (ranks after every member, adjacent to all members) ----
+    const int32_t* P;
+    int p;
+    {
+      int32_t last = sV[w][nv - 1];
+      int64_t b = g.ooff[last], e = g.ooff[last + 1];
+      if (nv == 1) {
+        P = g.oout + b;
+        p = (int)(e - b);
+        if (lane == 0) my_bytes += 4ull * (unsigned long long)p;
+      } else {
+        // candidates from the shortest member row (restricted to ranks > last)
+        int64_t cb = b, ce = e;
+        int srci = nv - 1;
+        for (int i = 0; i < nv - 1; ++i) {
+          int32_t v = sV[w][i];
+          int64_t rb = g.ooff[v], re = g.ooff[v + 1];
+          rb = lower_bound_dev64(g.oout, rb, re, last + 1);
+          if (re - rb < ce - cb) {
+            cb = rb;
+            ce = re;
+            srci = i;
+          }
+        }
+        int32_t* dst = (ce - cb) <= PSMEM ? sP[w] : scratch;
+        int cnt = 0;
+        for (int64_t base = cb; base < ce; base += 32) {
+          int64_t t = base + lane;
+          bool keep = false;
+          int32_t x = 0;
+          if (t < ce) {
+            x = __ldg(g.oout + t);
+            keep = true;
+            for (int i = 0; i < nv && keep; ++i) {
+              if (i == srci) continue;  // the row the candidates come from
+              int32_t v = sV[w][i];
+              keep = contains64(g.oout, g.ooff[v], g.ooff[v + 1], x);
+            }
+          }
+          unsigned bal = __ballot_sync(FULL, keep);
+          if (keep) dst[cnt + __popc(bal & ((1u << lane) - 1))] = x;
+          cnt += __popc(bal);
+        }
+        __syncwarp();
+        if (lane == 0) my_bytes += 4ull * (unsigned long long)(ce - cb) * nv;
+        P = dst;
+        p = cnt;
+      }
+    }
+
+    // ---- dequeue: prune (line 11), then result insertion (lines 6-10) ----
+    int32_t tau = ld_volatile(&cx.st->tau);
+    int bound = nv + p;
+    if (!cx.no_prune && bound < tau) {
+      if (lane == 0) ++my_pruned;
+      continue;
+    }
+    if (nv >= MAXD && p > 0) {
+      if (lane == 0) atomicOr(&cx.st->err, 1);
+      continue;
+    }
+    // a record that must be split reserves its children's staging slots first; if the
+    // staging array is full it goes back to the frontier untouched (re-dequeued later)
+    int64_t base_slot = 0;
+    if (p > BM) {
+      bool reserved = true;
+      if (lane == 0) {
+        base_slot = (int64_t)atomicAdd((unsigned long long*)&cx.st->stage_count,
+                                       (unsigned long long)p);
+        if (base_slot + p > cx.stage_cap) {
+          reserved = false;
+          int64_t ds = (int64_t)atomicAdd((unsigned long long*)&cx.st->defer_count, 1ull);
+          Rec* r = cx.deferred + ds;
+          r->nv = nv;
+          r->bound = bound;
+          for (int i = 0; i < nv; ++i) r->V[i] = sV[w][i];
+          --my_deq;
+        }
+      }
+      reserved = __shfl_sync(FULL, (int)reserved, 0);
+      base_slot = __shfl_sync(FULL, base_slot, 0);
+      if (!reserved) continue;
+    }
+    if (lane == 0 && nv >= tau) {
+      bool rel = true;
+      if (cx.maximal) rel = (p == 0) && is_maximal(g, sV[w], nv);
+      if (rel) add_result(cx, sV[w], nv, 0, nullptr);
+    }
+    if (p == 0) continue;
+
+    if (p <= BM) {
+      // ================= bitmap tail: finish the whole subtree in this warp =================
+      int32_t* sp = sP[w];
+      if (P != sp) {
+        for (int i = lane; i < p; i += 32) sp[i] = P[i];
+        __syncwarp();
+      }
+      const int32_t plast = sp[p - 1];
+      // row[i] = bits j > i with sp[j] in N+(sp[i])
+      for (int i = 0; i < p; ++i) {
+        int32_t v = sp[i];
+        int64_t rb = g.ooff[v], re = g.ooff[v + 1];
+        unsigned long long bits = 0;
+        int64_t scanned = 0;
+        for (int64_t base = rb; base < re; base += 32) {
+          int64_t t = base + lane;
+          int32_t x = t < re ? __ldg(g.oout + t) : INT32_MAX;
+          if (x <= plast) {
+            int j = lower_bound_dev(sp, i + 1, p, x);
+            if (j < p && sp[j] == x) bits |= 1ull << j;
+          }
+          scanned += 32;
+          // rows are sorted: stop once the whole chunk is past the last candidate
+          if (__all_sync(FULL, x > plast)) break;
+        }
+        unsigned lo = __reduce_or_sync(FULL, (unsigned)bits);
+        unsigned hi = __reduce_or_sync(FULL, (unsigned)(bits >> 32));
+        if (lane == 0) {
+          sRow[w][i] = ((unsigned long long)hi << 32) | lo;
+          my_bytes += 4ull * (unsigned long long)(scanned < re - rb ? scanned : re - rb);
+        }
+      }
+      __syncwarp();
+      // lane-parallel depth-first search: lane owns the children j = lane, lane + 32.
+      // Per-lane stack (local memory): stk[d] = untried candidates of the node at depth d,
+      // pick[d] = index in P of the vertex added at depth d (depth <= |P| <= 64).
+      bool limit_hit = false;
+      unsigned long long stk[BM];
+      uint8_t pick[BM + 1];
+      for (int j = lane; j < p; j += 32) {
+        int depth = 0;  // picks below the record minus one
+        pick[0] = (uint8_t)j;
+        unsigned long long X = sRow[w][j];
+        while (true) {
+          // node: record + pick[0..depth], candidates X
+          int size = nv + depth + 1;
+          ++my_exp;
+          int32_t t_now = ld_volatile(&cx.st->tau);
+          int bnd = size + __popcll(X);
+          bool expand_node = true;
+          if (!cx.no_prune && bnd < t_now) {
+            ++my_pruned;
+            expand_node = false;
+          } else if (size >= t_now) {
+            bool rel = true;
+            int32_t pick_ranks[BM];
+            for (int d = 0; d <= depth; ++d) pick_ranks[d] = sp[pick[d]];
+            if (cx.maximal) {
+              if (X != 0) rel = false;
+              else {
+                int32_t C[MAXD];
+                for (int i = 0; i < nv; ++i) C[i] = sV[w][i];
+                for (int d = 0; d <= depth; ++d) C[nv + d] = pick_ranks[d];
+                rel = is_maximal(g, C, size);
+              }
+            }
+            if (rel) add_result(cx, sV[w], nv, depth + 1, pick_ranks);
+          }
+          if (expand_node && X != 0 && size >= MAXD) {
+            limit_hit = true;
+            expand_node = false;
+          }
+          if (expand_node && X != 0) {
+            // descend into the lowest candidate, keep the rest for the siblings
+            int b = __ffsll((long long)X) - 1;
+            unsigned long long rest = X & (X - 1);
+            stk[depth] = rest;
+            ++depth;
+            pick[depth] = (uint8_t)b;
+            X = rest & sRow[w][b];
+            continue;
+          }
+          // back up to the next sibling that can still reach tau
+          bool done = false;
+          while (true) {
+            if (depth == 0) {
+              done = true;
+              break;
+            }
+            unsigned long long rest = stk[depth - 1];
+            int parent_size = nv + depth;  // size of the node whose children are iterated
+            int32_t t2 = ld_volatile(&cx.st->tau);
+            if (rest == 0 || (!cx.no_prune && parent_size + __popcll(rest) < t2)) {
+              --depth;
+              continue;
+            }
+            int b = __ffsll((long long)rest) - 1;
+            unsigned long long rest2 = rest & (rest - 1);
+            stk[depth - 1] = rest2;
+            pick[depth] = (uint8_t)b;
+            X = rest2 & sRow[w][b];
+            break;
+          }
+          if (done) break;
+        }
+      }
+      if (limit_hit) atomicOr(&cx.st->err, 1);
+      __syncwarp();
+      continue;
+    }
+
+    // ================= split: one child per d in P, pushed to the staging array =================
+    const int32_t plast = P[p - 1];
+    for (int j = 0; j < p; ++j) {
+      int32_t d = P[j];
+      int64_t rb = g.ooff[d], re = g.ooff[d + 1];
+      int64_t re2 = lower_bound_dev64(g.oout, rb, re, plast + 1);
+      int alen = p - j - 1;
+      int64_t blen = re2 - rb;
+      int c = 0;
+      if (alen > 0 && blen > 0) {
+        if (blen <= alen) {
+          for (int64_t t0 = rb; t0 < re2; t0 += 32) {
+            int64_t t = t0 + lane;
+            bool hit = false;
+            if (t < re2) {
+              int32_t x = __ldg(g.oout + t);
+              int q = lower_bound_dev(P, j + 1, p, x);
+              hit = q < p && P[q] == x;
+            }
+            c += __popc(__ballot_sync(FULL, hit));
+          }
+        } else {
+          for (int t0 = j + 1; t0 < p; t0 += 32) {
+            int t = t0 + lane;
+            bool hit = false;
+            if (t < p) hit = contains64(g.oout, rb, re2, P[t]);
+            c += __popc(__ballot_sync(FULL, hit));
+          }
+        }
+      }
+      if (lane == 0) {
+        ++my_exp;
+        my_bytes += 4ull * (unsigned long long)(alen + blen);
+        int32_t t_now = ld_volatile(&cx.st->tau);
+        int cb = nv + 1 + c;
+        if (!cx.no_prune && cb < t_now) {
+          ++my_pruned;
+        } else if (c == 0) {
+          // a leaf: the child is a clique with no extension; it is dequeued at once
+          ++my_deq;
+          int size = nv + 1;
+          if (size >= t_now) {
+            bool rel = true;
+            if (cx.maximal) {
+              int32_t C[MAXD];
+              for (int i = 0; i < nv; ++i) C[i] = sV[w][i];
+              C[nv] = d;
+              rel = is_maximal(g, C, size);
+            }
+            if (rel) add_result(cx, sV[w], nv, 1, &d);
+          }
+        } else {
+          Rec* r = cx.stage + base_slot + j;
+          r->nv = nv + 1;
+          r->bound = cb;
+          for (int i = 0; i < nv; ++i) r->V[i] = sV[w][i];
+          r->V[nv] = d;
+        }
+      }
+    }
+    __syncwarp();
+  }
+  if (lane == 0) {
+    atomicAdd(&cx.st->dequeued, my_deq);
+    atomicAdd(&cx.st->adj_bytes, my_bytes);
+  }
+  // per-lane counters (lanes count bitmap-tail nodes)
+  for (int o = 16; o; o >>= 1) {
+    my_exp += __shfl_xor_sync(FULL, my_exp, o);
+    my_pruned += __shfl_xor_sync(FULL, my_pruned, o);
+  }
+  if (lane == 0) {
+    atomicAdd(&cx.st->expansions, my_exp);
+    atomicAdd(&cx.st->pruned, my_pruned);
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// frontier plumbing
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ int bucket_of(int32_t bound) { return bound >= NB - 1 ? NB - 1 : bound; }
+
+__global__ void k_seed_bounds(DevGraph g, int32_t* keys, int32_t* vals) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < g.n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    keys[r] = 1 + (int32_t)(g.ooff[r + 1] - g.ooff[r]);
+    vals[r] = (int32_t)r;
+  }
+}
+
+__global__ void k_bucket_hist(const int32_t* keys, int64_t n, int32_t* hist) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&hist[bucket_of(keys[i])], 1);
+}
+
+__global__ void k_stage_hist(const Rec* stage, int64_t cnt, int32_t* hist) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if (stage[i].nv > 0) atomicAdd(&hist[bucket_of(stage[i].bound)], 1);
+}
+
+struct BucketPtrs {
+  Rec* base[NB];
+  int64_t fill[NB];  // current counts before the scatter
+};
+
+__global__ void k_stage_scatter(const Rec* stage, int64_t cnt, BucketPtrs bp, int32_t* cursor) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (stage[i].nv <= 0) continue;
+    int b = bucket_of(stage[i].bound);
+    int64_t pos = bp.fill[b] + atomicAdd(&cursor[b], 1);
+    bp.base[b][pos] = stage[i];
+  }
+}
+
+__global__ void k_clear_stage(Rec* stage, int64_t cnt) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt;
+       i += (int64_t)gridDim.x * blockDim.x)
+    stage[i].nv = 0;
+}
+
+// ---- final selection ----
+__global__ void k_select(const Rec* res, int64_t cnt, int32_t tau, const DevGraph g,
+                         int32_t* flag, int32_t* outV, int32_t* outN, int32_t* nsel) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int c = res[i].nv;
+    if (c < tau) continue;
+    int pos = atomicAdd(nsel, 1);
+    int32_t ids[MAXD];
+    for (int t = 0; t < c; ++t) ids[t] = __ldg(g.vert_of + res[i].V[t]);
+    for (int a = 1; a < c; ++a) {  // insertion sort (c <= 32)
+      int32_t x = ids[a];
+      int b = a - 1;
+      while (b >= 0 && ids[b] > x) {
+        ids[b + 1] = ids[b];
+        --b;
+      }
+      ids[b + 1] = x;
+    }
+    for (int t = 0; t < MAXD; ++t) outV[(int64_t)pos * MAXD + t] = t < c ? ids[t] : -1;
+    outN[pos] = c;
+  }
+}
+
+__global__ void k_gather_col(const int32_t* V, const int32_t* N, const int32_t* perm, int32_t n,
+                             int col, uint32_t* key) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t r = perm[i];
+    key[i] = col < 0 ? (uint32_t)(MAXD - N[r]) : (uint32_t)(V[(int64_t)r * MAXD + col] + 1);
+  }
+}
+
+__global__ void k_iota(int32_t* a, int32_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    a[i] = (int32_t)i;
+}
+
+__global__ void k_emit(const int32_t* V, const int32_t* N, const int32_t* perm, int32_t count,
+                       int32_t* outV, const int32_t* outOff, int64_t* outScore) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t r = perm[i];
+    int c = N[r];
+    outScore[i] = c;
+    for (int t = 0; t < c; ++t) outV[outOff[i] + t] = V[(int64_t)r * MAXD + t];
+  }
+}
+
+__global__ void k_sizes(const int32_t* N, const int32_t* perm, int32_t count, int32_t* sz) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    sz[i] = N[perm[i]];
+}
+
+inline int grid_for(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, 1 << 20));
+}
+
+struct HostBucket {
+  DBuf<Rec> dev;            // device records [0, count)
+  int64_t count = 0;
+  std::vector<Rec*> spilled;          // pinned host chunks
+  std::vector<int64_t> spilled_n;
+  int64_t spilled_total = 0;
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap,
+                  cudaStream_t s, nuri_result** out) {
+  int64_t launches = 0;
+  const DevGraph& g = G->d;
+  DevTimer timer(s);
+  const bool maximal = flags & NURI_CLIQUE_MAXIMAL;
+  const bool no_prune = flags & NURI_NO_PRUNE;
+  const bool keep_ties = flags & NURI_KEEP_TIES;
+  if (frontier_cap <= 0) frontier_cap = 1 << 22;
+  const int n = g.n;
+
+  const int grid = sm_count() * 6;  // resident CTAs: 6 x 4 warps per SM
+  const int total_warps = grid * WARPS;
+  const int64_t stage_cap = std::max<int64_t>(1 << 16, (int64_t)g.max_out * 8);
+
+  DBuf<QState> st;
+  st.alloc(1, s);
+  DBuf<int32_t> pscratch;
+  if (g.max_out > PSMEM) pscratch.alloc((int64_t)total_warps * g.max_out, s);
+  DBuf<Rec> stage, deferred, inbuf;
+  stage.alloc(stage_cap, s);
+  ++launches;
+  k_clear_stage<<<grid_for(stage_cap), 256, 0, s>>>(stage.p, stage_cap);
+  int64_t res_cap = std::max<int64_t>(1 << 16, (int64_t)k * 64);
+  // initial result-buffer capacity override (exercises the overflow re-run in tests)
+  if (const char* e = getenv("NURI_RESULT_CAP")) res_cap = std::max<int64_t>(1, atoll(e));
+  int32_t tau_init = INT32_MIN;
+  int restarts = 0;
+  std::vector<HostBucket> buckets(NB);
+
+  // seeds: sorted by bound descending
+  DBuf<int32_t> skeys, svals, skeys2, svals2, bhist;
+  skeys.alloc(std::max(n, 1), s);
+  svals.alloc(std::max(n, 1), s);
+  skeys2.alloc(std::max(n, 1), s);
+  svals2.alloc(std::max(n, 1), s);
+  bhist.alloc(NB, s);
+  std::vector<int32_t> seed_hist(NB, 0);
+  if (n > 0) {
+    ++launches;
+    k_seed_bounds<<<grid_for(n), 256, 0, s>>>(g, skeys.p, svals.p);
+    size_t tb = 0;
+    cub::DeviceRadixSort::SortPairsDescending(nullptr, tb, skeys.p, skeys2.p, svals.p, svals2.p,
+                                              n, 0, 32, s);
+    DBuf<uint8_t> tmp;
+    tmp.alloc(tb, s);
+    NURI_CUDA(cub::DeviceRadixSort::SortPairsDescending(tmp.p, tb, skeys.p, skeys2.p, svals.p,
+                                                        svals2.p, n, 0, 32, s));
+    NURI_CUDA(cudaMemsetAsync(bhist.p, 0, sizeof(int32_t) * NB, s));
+    ++launches;
+    k_bucket_hist<<<grid_for(n), 256, 0, s>>>(skeys2.p, n, bhist.p);
+    NURI_CUDA(cudaMemcpyAsync(seed_hist.data(), bhist.p, sizeof(int32_t) * NB,
+                              cudaMemcpyDeviceToHost, s));
+    NURI_CUDA(cudaStreamSynchronize(s));
+  }
+  // seed ranges per bucket (seeds are sorted by descending bound)
+  std::vector<int64_t> seed_lo(NB), seed_hi(NB);
+  {
+    int64_t pos = 0;
+    for (int b = NB - 1; b >= 0; --b) {
+      seed_lo[b] = pos;
+      pos += seed_hist[b];
+      seed_hi[b] = pos;
+    }
+  }
+
+  QState hs;
+  nuri_stats stats;
+  memset(&stats, 0, sizeof(stats));
+  cudaEvent_t ev0, ev1;
+  NURI_CUDA(cudaEventCreate(&ev0));
+  NURI_CUDA(cudaEventCreate(&ev1));
+  struct EvGuard {
+    cudaEvent_t a, b;
+    ~EvGuard() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+  } evg{ev0, ev1};
+
+  DBuf<Rec> res;
+  while (true) {  // one pass; repeated only after a result-buffer overflow
+    res.alloc(res_cap, s);
+    memset(&hs, 0, sizeof(hs));
+    hs.tau = tau_init;
+    NURI_CUDA(cudaMemcpyAsync(st.p, &hs, sizeof(hs), cudaMemcpyHostToDevice, s));
+    for (auto& b : buckets) {
+      b.count = 0;
+      for (Rec* p : b.spilled) cudaFreeHost(p);
+      b.spilled.clear();
+      b.spilled_n.clear();
+      b.spilled_total = 0;
+    }
+    std::vector<int64_t> seed_next(seed_lo);
+    Ctx cx;
+    cx.g = g;
+    cx.st = st.p;
+    cx.res = res.p;
+    cx.res_cap = res_cap;
+    cx.stage = stage.p;
+    cx.stage_cap = stage_cap;
+    cx.pscratch = pscratch.p;
+    cx.pscratch_stride = g.max_out;
+    cx.k = k;
+    cx.maximal = maximal;
+    cx.no_prune = no_prune;
+    int64_t rounds = 0;
+    int64_t seed_chunk = std::max<int64_t>(total_warps, 1024);
+
+    while (true) {
+      NURI_CUDA(cudaMemcpyAsync(&hs, st.p, sizeof(hs), cudaMemcpyDeviceToHost, s));
+      NURI_CUDA(cudaStreamSynchronize(s));
+      if (hs.err & 1) NURI_FAIL(NURI_ERR_LIMIT, "nuri_topk_cliques: a clique exceeds %d vertices", MAXD);
+      int32_t tau = hs.tau;
+      // highest bucket with pending seeds or records
+      int b_seed = -1, b_front = -1;
+      for (int b = NB - 1; b >= 0; --b)
+        if (seed_next[b] < seed_hi[b]) {
+          b_seed = b;
+          break;
+        }
+      for (int b = NB - 1; b >= 0; --b)
+        if (buckets[b].count + buckets[b].spilled_total > 0) {
+          b_front = b;
+          break;
+        }
+      int best = std::max(b_seed, b_front);
+      if (best < 0) break;
+      if (!no_prune && best < NB - 1 && best < tau) break;  // every remaining bound < tau
+
+      NURI_CUDA(cudaMemsetAsync(&st.p->work_next, 0, sizeof(int64_t), s));
+      NURI_CUDA(cudaMemsetAsync(&st.p->stage_count, 0, sizeof(int64_t), s));
+      NURI_CUDA(cudaMemsetAsync(&st.p->defer_count, 0, sizeof(int64_t), s));
+      int64_t nin = 0;
+      int src_bucket = -1;
+      if (b_front >= b_seed) {
+        HostBucket& hb = buckets[b_front];
+        src_bucket = b_front;
+        if (hb.count == 0) {  // reload one spilled chunk
+          Rec* hp = hb.spilled.back();
+          int64_t hn = hb.spilled_n.back();
+          hb.spilled.pop_back();
+          hb.spilled_n.pop_back();
+          hb.spilled_total -= hn;
+          if ((int64_t)hb.dev.n < hn) hb.dev.alloc(hn, s);
+          NURI_CUDA(cudaMemcpyAsync(hb.dev.p, hp, sizeof(Rec) * hn, cudaMemcpyHostToDevice, s));
+          NURI_CUDA(cudaStreamSynchronize(s));
+          cudaFreeHost(hp);
+          hb.count = hn;
+          stats.reloaded += hn;
+        }
+        nin = std::min<int64_t>(hb.count, std::max<int64_t>(total_warps * 2, 4096));
+        if ((int64_t)inbuf.n < nin) inbuf.alloc(std::max<int64_t>(nin, 4096), s);
+        NURI_CUDA(cudaMemcpyAsync(inbuf.p, hb.dev.p + (hb.count - nin), sizeof(Rec) * nin,
+                                  cudaMemcpyDeviceToDevice, s));
+        hb.count -= nin;
+        if ((int64_t)deferred.n < nin) deferred.alloc(std::max<int64_t>(nin, 4096), s);
+        cx.deferred = deferred.p;
+        NURI_CUDA(cudaEventRecord(ev0, s));
+        ++launches;
+        k_clique_expand<<<grid, WARPS * 32, 0, s>>>(cx, inbuf.p, nullptr, nin);
+        NURI_CUDA(cudaEventRecord(ev1, s));
+      } else {
+        int64_t lo = seed_next[b_seed];
+        nin = std::min<int64_t>(seed_hi[b_seed] - lo, seed_chunk);
+        seed_next[b_seed] += nin;
+        seed_chunk = std::min<int64_t>(seed_chunk * 2, 1 << 20);
+        if ((int64_t)deferred.n < nin) deferred.alloc(std::max<int64_t>(nin, 4096), s);
+        cx.deferred = deferred.p;
+        NURI_CUDA(cudaEventRecord(ev0, s));
+        ++launches;
+        k_clique_expand<<<grid, WARPS * 32, 0, s>>>(cx, nullptr, svals2.p + lo, nin);
+        NURI_CUDA(cudaEventRecord(ev1, s));
+      }
+      NURI_CUDA(cudaGetLastError());
+      ++rounds;
+      // staging (children) and deferred parents -> buckets, by bound
+      int64_t scnt = 0, dcnt = 0;
+      NURI_CUDA(cudaMemcpyAsync(&scnt, &st.p->stage_count, 8, cudaMemcpyDeviceToHost, s));
+      NURI_CUDA(cudaMemcpyAsync(&dcnt, &st.p->defer_count, 8, cudaMemcpyDeviceToHost, s));
+      NURI_CUDA(cudaStreamSynchronize(s));
+      {
+        float ms = 0.f;
+        NURI_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
+        stats.expand_ms += ms;
+        stats.expand_launches += 1;
+      }
+      scnt = std::min(scnt, stage_cap);
+      auto scatter = [&](Rec* arr, int64_t cnt) {
+        if (cnt <= 0) return;
+        std::vector<int32_t> sh(NB, 0);
+        NURI_CUDA(cudaMemsetAsync(bhist.p, 0, sizeof(int32_t) * NB, s));
+        ++launches;
+        k_stage_hist<<<grid_for(cnt), 256, 0, s>>>(arr, cnt, bhist.p);
+        NURI_CUDA(cudaMemcpyAsync(sh.data(), bhist.p, sizeof(int32_t) * NB,
+                                  cudaMemcpyDeviceToHost, s));
+        NURI_CUDA(cudaStreamSynchronize(s));
+        BucketPtrs bp;
+        for (int b = 0; b < NB; ++b) {
+          HostBucket& hb = buckets[b];
+          int64_t need = hb.count + sh[b];
+          if (need > (int64_t)hb.dev.n) {
+            DBuf<Rec> nb;
+            nb.alloc(std::max<int64_t>(need * 2, 1024), s);
+            if (hb.count)
+              NURI_CUDA(cudaMemcpyAsync(nb.p, hb.dev.p, sizeof(Rec) * hb.count,
+                                        cudaMemcpyDeviceToDevice, s));
+            hb.dev = std::move(nb);
+          }
+          bp.base[b] = hb.dev.p;
+          bp.fill[b] = hb.count;
+        }
+        NURI_CUDA(cudaMemsetAsync(bhist.p, 0, sizeof(int32_t) * NB, s));
+        ++launches;
+        k_stage_scatter<<<grid_for(cnt), 256, 0, s>>>(arr, cnt, bp, bhist.p);
+        ++launches;
+        k_clear_stage<<<grid_for(cnt), 256, 0, s>>>(arr, cnt);
+        for (int b = 0; b < NB; ++b) buckets[b].count += sh[b];
+      };
+      scatter(stage.p, scnt);
+      scatter(deferred.p, dcnt);
+      (void)src_bucket;
+      // spill the lowest buckets while the device frontier is above its capacity
+      int64_t total = 0;
+      for (auto& hb : buckets) total += hb.count;
+      for (int b = 0; b < NB && total > frontier_cap; ++b) {
+        HostBucket& hb = buckets[b];
+        if (hb.count == 0) continue;
+        if (!no_prune && b < tau && b < NB - 1) {  // dominated: drop instead of spilling
+          total -= hb.count;
+          stats.pruned += hb.count;
+          hb.count = 0;
+          continue;
+        }
+        Rec* hp = nullptr;
+        if (cudaMallocHost((void**)&hp, sizeof(Rec) * hb.count) != cudaSuccess)
+          NURI_FAIL(NURI_ERR_OOM, "nuri_topk_cliques: pinned host allocation failed");
+        NURI_CUDA(cudaMemcpyAsync(hp, hb.dev.p, sizeof(Rec) * hb.count, cudaMemcpyDeviceToHost, s));
+        hb.spilled.push_back(hp);
+        hb.spilled_n.push_back(hb.count);
+        hb.spilled_total += hb.count;
+        stats.spilled += hb.count;
+        total -= hb.count;
+        hb.count = 0;
+      }
+      NURI_CUDA(cudaStreamSynchronize(s));
+    }
+    // drop what is left (every remaining bound < tau)
+    for (auto& b : buckets) {
+      for (Rec* p : b.spilled) cudaFreeHost(p);
+      b.spilled.clear();
+      b.spilled_n.clear();
+      b.spilled_total = 0;
+      b.count = 0;
+    }
+    stats.rounds += rounds;
+    if (hs.res_count > res_cap) {
+      // every result with size >= tau_final was counted: re-run with that threshold and room
+      int64_t need = 0;
+      for (int c = std::max(hs.tau, 0); c <= MAXD; ++c) need += hs.hist[c];
+      res_cap = std::max<int64_t>(need + 1024, res_cap);
+      tau_init = hs.tau;
+      ++restarts;
+      continue;
+    }
+    break;
+  }
+
+  // ---- top-k merge: rows with size >= tau, ordered by (size desc, ids lex asc) ----
+  int64_t cnt = hs.res_count;
+  int32_t tau = hs.tau;
+  DBuf<int32_t> selV, selN, nsel, flag;
+  selV.alloc(std::max<int64_t>(cnt, 1) * MAXD, s);
+  selN.alloc(std::max<int64_t>(cnt, 1), s);
+  nsel.alloc(1, s);
+  flag.alloc(1, s);
+  NURI_CUDA(cudaMemsetAsync(nsel.p, 0, 4, s));
+  if (cnt > 0) { ++launches; k_select<<<grid_for(cnt), 256, 0, s>>>(res.p, cnt, tau, g, flag.p, selV.p, selN.p, nsel.p); }
+  int32_t ns = 0;
+  NURI_CUDA(cudaMemcpyAsync(&ns, nsel.p, 4, cudaMemcpyDeviceToHost, s));
+  NURI_CUDA(cudaStreamSynchronize(s));
+  int maxc = 0;
+  for (int c = MAXD; c >= 1; --c)
+    if (hs.hist[c] > 0) {
+      maxc = c;
+      break;
+    }
+  DBuf<int32_t> perm, perm2;
+  DBuf<uint32_t> key, key2;
+  perm.alloc(std::max(ns, 1), s);
+  perm2.alloc(std::max(ns, 1), s);
+  key.alloc(std::max(ns, 1), s);
+  key2.alloc(std::max(ns, 1), s);
+  if (ns > 0) {
+    ++launches;
+    k_iota<<<grid_for(ns), 256, 0, s>>>(perm.p, ns);
+    size_t tb = 0;
+    cub::DeviceRadixSort::SortPairs(nullptr, tb, key.p, key2.p, perm.p, perm2.p, ns, 0, 32, s);
+    DBuf<uint8_t> tmp;
+    tmp.alloc(tb, s);
+    // least significant column first; the size key last (stable passes)
+    for (int col = maxc - 1; col >= -1; --col) {
+      ++launches;
+      k_gather_col<<<grid_for(ns), 256, 0, s>>>(selV.p, selN.p, perm.p, ns, col, key.p);
+      NURI_CUDA(cub::DeviceRadixSort::SortPairs(tmp.p, tb, key.p, key2.p, perm.p, perm2.p, ns,
+                                                0, 32, s));
+      std::swap(perm.p, perm2.p);
+    }
+  }
+  int32_t count = ns;
+  if (!keep_ties) count = std::min(count, k);
+  // row sizes on the host for the offsets
+  std::vector<int32_t> sizes(count);
+  DBuf<int32_t> dsz;
+  dsz.alloc(std::max(count, 1), s);
+  if (count > 0) {
+    ++launches;
+    k_sizes<<<grid_for(count), 256, 0, s>>>(selN.p, perm.p, count, dsz.p);
+    NURI_CUDA(cudaMemcpyAsync(sizes.data(), dsz.p, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, s));
+    NURI_CUDA(cudaStreamSynchronize(s));
+  }
+  int64_t nverts = 0;
+  for (int i = 0; i < count; ++i) nverts += sizes[i];
+  nuri_result* r = new_result(0, count, nverts, 0, false);
+  r->vert_off[0] = 0;
+  for (int i = 0; i < count; ++i) r->vert_off[i + 1] = r->vert_off[i] + sizes[i];
+  r->edge_off[0] = 0;
+  for (int i = 0; i < count; ++i) r->edge_off[i + 1] = 0;
+  if (count > 0) {
+    DBuf<int32_t> dOff, dV;
+    DBuf<int64_t> dS;
+    dOff.alloc(count + 1, s);
+    dV.alloc(std::max<int64_t>(nverts, 1), s);
+    dS.alloc(count, s);
+    NURI_CUDA(cudaMemcpyAsync(dOff.p, r->vert_off, sizeof(int32_t) * (count + 1),
+                              cudaMemcpyHostToDevice, s));
+    ++launches;
+    k_emit<<<grid_for(count), 256, 0, s>>>(selV.p, selN.p, perm.p, count, dV.p, dOff.p, dS.p);
+    NURI_CUDA(cudaMemcpyAsync(r->verts, dV.p, sizeof(int32_t) * nverts, cudaMemcpyDeviceToHost, s));
+    NURI_CUDA(cudaMemcpyAsync(r->score, dS.p, sizeof(int64_t) * count, cudaMemcpyDeviceToHost, s));
+    NURI_CUDA(cudaStreamSynchronize(s));
+  }
+  stats.expansions += (int64_t)hs.expansions;
+  stats.pruned += (int64_t)hs.pruned;
+  stats.dequeued += (int64_t)hs.dequeued;
+  stats.adj_bytes += (int64_t)hs.adj_bytes;
+  stats.results_stored = hs.res_count;
+  stats.threshold = hs.tau == INT32_MIN ? INT64_MIN : hs.tau;
+  stats.restarts = restarts;
+  stats.device_ms = timer.stop();
+  stats.launches = launches;
+  r->stats = stats;
+  *out = r;
+}
+
+}  // namespace nuri

@@ -1,0 +1,598 @@
+// Device graph construction: the engine loads the data graph into memory (Section 5) and runs
+// each vertex's index initialize() at load time (Section 4.3, Listing 3).
+//
+// Steps (all on the device, stream-ordered):
+//   1. validate ids, expand each input pair to both directions, drop self-loops
+//   2. radix-sort the 64-bit (row, col) keys, drop duplicates -> undirected CSR (sorted rows)
+//   3. degree orientation for cliques: rank = position in (degree, id) order; out-rows in rank
+//      space keep only neighbours of larger rank (bounded out-degree on power-law graphs)
+//   4. label segments: each row grouped by neighbour label, each group sorted by score desc
+//   5. hop/label max index, H rounds of a gather-max over neighbours
+#include <cub/cub.cuh>
+
+#include "nuri_internal.cuh"
+
+namespace nuri {
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int blocks_for(int64_t n, int threads = kThreads) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > (1ll << 30)) b = 1ll << 30;
+  return (int)b;
+}
+
+inline int bitlen(uint64_t x) {
+  int b = 0;
+  while (x) {
+    ++b;
+    x >>= 1;
+  }
+  return b;
+}
+
+__global__ void k_validate(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                           int64_t m, int32_t n, int32_t* bad) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t a = src[i], b = dst[i];
+    if (a < 0 || a >= n || b < 0 || b >= n) atomicExch(bad, 1);
+  }
+}
+
+// both directions of every pair; a self-loop becomes the sentinel row n
+__global__ void k_expand_pairs(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                               int64_t m, int32_t n, uint64_t* __restrict__ keys) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t a = (uint32_t)src[i], b = (uint32_t)dst[i];
+    uint64_t sent = (uint64_t)(uint32_t)n << 32;
+    keys[2 * i] = a == b ? sent : ((uint64_t)a << 32) | b;
+    keys[2 * i + 1] = a == b ? sent : ((uint64_t)b << 32) | a;
+  }
+}
+
+__global__ void k_split_keys(const uint64_t* __restrict__ keys, int64_t nnz,
+                             int32_t* __restrict__ adj, int32_t* __restrict__ deg) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nnz;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t k = keys[i];
+    adj[i] = (int32_t)(uint32_t)k;
+    atomicAdd(&deg[(uint32_t)(k >> 32)], 1);
+  }
+}
+
+__global__ void k_rank_keys(const int32_t* __restrict__ deg, int32_t n,
+                            uint64_t* __restrict__ keys) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    keys[i] = ((uint64_t)(uint32_t)deg[i] << 32) | (uint32_t)i;
+}
+
+__global__ void k_rank_split(const uint64_t* __restrict__ keys, int32_t n,
+                             int32_t* __restrict__ vert_of, int32_t* __restrict__ rank_of) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    int32_t v = (int32_t)(uint32_t)keys[r];
+    vert_of[r] = v;
+    rank_of[v] = (int32_t)r;
+  }
+}
+
+// one key per directed entry whose target has the larger rank; the rest become sentinels
+__global__ void k_orient_keys(const uint64_t* __restrict__ ckeys, int64_t nnz,
+                              const int32_t* __restrict__ rank_of, int32_t n,
+                              uint64_t* __restrict__ okeys) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nnz;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t k = ckeys[i];
+    int32_t rv = rank_of[(uint32_t)(k >> 32)], ru = rank_of[(uint32_t)k];
+    okeys[i] = rv < ru ? (((uint64_t)(uint32_t)rv << 32) | (uint32_t)ru)
+                       : ((uint64_t)(uint32_t)n << 32);
+  }
+}
+
+__global__ void k_orient_split(const uint64_t* __restrict__ okeys, int64_t cnt,
+                               int32_t* __restrict__ oout, int32_t* __restrict__ odeg) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t k = okeys[i];
+    oout[i] = (int32_t)(uint32_t)k;
+    atomicAdd(&odeg[(uint32_t)(k >> 32)], 1);
+  }
+}
+
+__global__ void k_max_i32(const int32_t* __restrict__ a, int64_t n, int32_t* out) {
+  int32_t best = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    best = max(best, a[i]);
+  for (int o = 16; o; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, best);
+}
+
+__global__ void k_max_u8(const uint8_t* __restrict__ a, int64_t n, int32_t* out) {
+  int32_t best = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    best = max(best, (int32_t)a[i]);
+  for (int o = 16; o; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, best);
+}
+
+__global__ void k_min_i32(const int32_t* __restrict__ a, int64_t n, int32_t* out) {
+  int32_t best = INT32_MAX;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    best = min(best, a[i]);
+  for (int o = 16; o; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if ((threadIdx.x & 31) == 0) atomicMin(out, best);
+}
+
+// label segments: secondary key (score desc, id asc), value = (row << 32 | col)
+__global__ void k_seg_keys(const uint64_t* __restrict__ ckeys, int64_t nnz,
+                           const int32_t* __restrict__ score, uint64_t* __restrict__ skey,
+                           uint64_t* __restrict__ sval) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nnz;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t k = ckeys[i];
+    uint32_t u = (uint32_t)k;
+    uint32_t inv = (uint32_t)(INT32_MAX - score[u]);  // score >= 0 -> larger score first
+    skey[i] = ((uint64_t)inv << 32) | u;
+    sval[i] = k;
+  }
+}
+
+__global__ void k_seg_primary(const uint64_t* __restrict__ sval, int64_t nnz,
+                              const uint8_t* __restrict__ labels, int32_t L,
+                              uint64_t* __restrict__ pkey) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nnz;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t k = sval[i];
+    uint32_t v = (uint32_t)(k >> 32), u = (uint32_t)k;
+    pkey[i] = (uint64_t)v * (uint64_t)L + labels[u];
+  }
+}
+
+__global__ void k_seg_fill(const uint64_t* __restrict__ pkey, const uint64_t* __restrict__ sval,
+                           int64_t nnz, const int32_t* __restrict__ score,
+                           int2* __restrict__ seg, int32_t* __restrict__ segcnt) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nnz;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t u = (uint32_t)sval[i];
+    seg[i] = make_int2((int32_t)u, score[u]);
+    atomicAdd(&segcnt[pkey[i]], 1);
+  }
+}
+
+__global__ void k_i32_to_i64(const int32_t* __restrict__ a, int64_t n, int64_t* __restrict__ b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = a[i];
+}
+
+__global__ void k_gmax(const uint8_t* __restrict__ labels, const int32_t* __restrict__ score,
+                       int32_t n, int32_t* __restrict__ gmax) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    atomicMax(&gmax[labels[i]], score[i]);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+// Hop/label max index (Section 4.3, Listing 3), cumulative-hop reading:
+//   idx_h(v)[l] = max over x in N(v) of max(own(x)[l], idx_{h-1}(x)[l]),
+//   own(x)[l] = score(x) if label(x) == l else -1, idx_0 = -1.
+// i.e. the max score of a label-l vertex reachable from v by a walk of 1..h edges.
+// One warp per vertex: lanes are split into 32/L groups that take different neighbours, each
+// lane of a group owns one label, and the groups are reduced with shuffles.  Vertices with
+// degree above kHeavy get a whole CTA (one warp per neighbour slice + shared reduction).
+// HBM traffic per round: the CSR row (4 B per entry) plus the L-vector of each neighbour
+// (4*L B per entry, gathered), plus the output row.
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+constexpr int kHeavy = 2048;
+
+template <int LP>
+__global__ void __launch_bounds__(256) k_hop_round_light(
+    const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+    const uint8_t* __restrict__ labels, const int32_t* __restrict__ score,
+    const int32_t* __restrict__ prev, int32_t n, int32_t L, int32_t* __restrict__ cur) {
+  constexpr int G = 32 / LP;  // neighbours per step
+  const int lane = threadIdx.x & 31;
+  const int grp = lane / LP, l = lane % LP;
+  const bool active = l < L;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = warp; v < n; v += nwarps) {
+    int64_t b = off[v], e = off[v + 1];
+    if (e - b > kHeavy) continue;  // handled by the CTA kernel
+    int32_t acc = -1;
+    if (active)
+      for (int64_t i = b + grp; i < e; i += G) {
+        int32_t x = __ldg(adj + i);
+        int32_t own = (__ldg(labels + x) == l) ? __ldg(score + x) : -1;
+        int32_t p = prev ? __ldg(prev + (int64_t)x * L + l) : -1;
+        acc = max(acc, max(own, p));
+      }
+#pragma unroll
+    for (int o = LP; o < 32; o <<= 1) acc = max(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+    if (grp == 0 && active) cur[(int64_t)v * L + l] = acc;
+  }
+}
+
+template <int LP>
+__global__ void __launch_bounds__(512) k_hop_round_heavy(
+    const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+    const uint8_t* __restrict__ labels, const int32_t* __restrict__ score,
+    const int32_t* __restrict__ prev, const int32_t* __restrict__ heavy, int32_t nheavy,
+    int32_t L, int32_t* __restrict__ cur) {
+  constexpr int G = 32 / LP;
+  __shared__ int32_t red[16][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int grp = lane / LP, l = lane % LP;
+  const bool active = l < L;
+  for (int32_t hi = blockIdx.x; hi < nheavy; hi += gridDim.x) {
+    int32_t v = heavy[hi];
+    int64_t b = off[v], e = off[v + 1];
+    int32_t acc = -1;
+    if (active)
+      for (int64_t i = b + (int64_t)w * G + grp; i < e; i += (int64_t)nw * G) {
+        int32_t x = __ldg(adj + i);
+        int32_t own = (__ldg(labels + x) == l) ? __ldg(score + x) : -1;
+        int32_t p = prev ? __ldg(prev + (int64_t)x * L + l) : -1;
+        acc = max(acc, max(own, p));
+      }
+#pragma unroll
+    for (int o = LP; o < 32; o <<= 1) acc = max(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+    red[w][lane] = acc;
+    __syncthreads();
+    if (w == 0) {
+      int32_t a = red[0][lane];
+      for (int j = 1; j < nw; ++j) a = max(a, red[j][lane]);
+      if (lane < L && lane < LP) cur[(int64_t)v * L + lane] = a;
+    }
+    __syncthreads();
+  }
+}
+
+// general L (any label count): one thread per (v, l) pair, serial over the row
+__global__ void k_hop_round_generic(const int64_t* __restrict__ off,
+                                    const int32_t* __restrict__ adj,
+                                    const uint8_t* __restrict__ labels,
+                                    const int32_t* __restrict__ score,
+                                    const int32_t* __restrict__ prev, int32_t n, int32_t L,
+                                    int32_t* __restrict__ cur) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)n * L;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t v = t / L;
+    int l = (int)(t % L);
+    int32_t acc = -1;
+    for (int64_t i = off[v]; i < off[v + 1]; ++i) {
+      int32_t x = adj[i];
+      int32_t own = labels[x] == l ? score[x] : -1;
+      int32_t p = prev ? prev[(int64_t)x * L + l] : -1;
+      acc = max(acc, max(own, p));
+    }
+    cur[t] = acc;
+  }
+}
+
+__global__ void k_collect_heavy(const int64_t* __restrict__ off, int32_t n,
+                                int32_t* __restrict__ heavy, int32_t* __restrict__ cnt) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    if (off[v + 1] - off[v] > kHeavy) heavy[atomicAdd(cnt, 1)] = (int32_t)v;
+}
+
+template <int LP>
+void hop_rounds_t(const DevGraph& d, const int32_t* score, int32_t H, int32_t* idx,
+                  const int32_t* heavy, int32_t nheavy, cudaStream_t s) {
+  int grid = sm_count() * 8;
+  for (int h = 1; h <= H; ++h) {
+    const int32_t* prev = h == 1 ? nullptr : idx + (int64_t)(h - 2) * d.n * d.L;
+    int32_t* cur = idx + (int64_t)(h - 1) * d.n * d.L;
+    k_hop_round_light<LP><<<grid, 256, 0, s>>>(d.off, d.adj, d.labels, score, prev, d.n, d.L,
+                                               cur);
+    if (nheavy)
+      k_hop_round_heavy<LP><<<std::min(nheavy, sm_count() * 4), 512, 0, s>>>(
+          d.off, d.adj, d.labels, score, prev, heavy, nheavy, d.L, cur);
+  }
+}
+
+}  // namespace
+
+void build_hop_index(const DevGraph& d, const int32_t* score, int32_t H, int32_t* idx,
+                     cudaStream_t s) {
+  if (H <= 0 || d.n == 0) return;
+  DBuf<int32_t> heavy, cnt;
+  heavy.alloc(d.n, s);
+  cnt.alloc(1, s);
+  NURI_CUDA(cudaMemsetAsync(cnt.p, 0, 4, s));
+  k_collect_heavy<<<blocks_for(d.n), kThreads, 0, s>>>(d.off, d.n, heavy.p, cnt.p);
+  int32_t nheavy = 0;
+  NURI_CUDA(cudaMemcpyAsync(&nheavy, cnt.p, 4, cudaMemcpyDeviceToHost, s));
+  NURI_CUDA(cudaStreamSynchronize(s));
+  if (d.L <= 1) hop_rounds_t<1>(d, score, H, idx, heavy.p, nheavy, s);
+  else if (d.L <= 2) hop_rounds_t<2>(d, score, H, idx, heavy.p, nheavy, s);
+  else if (d.L <= 4) hop_rounds_t<4>(d, score, H, idx, heavy.p, nheavy, s);
+  else if (d.L <= 8) hop_rounds_t<8>(d, score, H, idx, heavy.p, nheavy, s);
+  else if (d.L <= 16) hop_rounds_t<16>(d, score, H, idx, heavy.p, nheavy, s);
+  else if (d.L <= 32) hop_rounds_t<32>(d, score, H, idx, heavy.p, nheavy, s);
+  else
+    for (int h = 1; h <= H; ++h) {
+      const int32_t* prev = h == 1 ? nullptr : idx + (int64_t)(h - 2) * d.n * d.L;
+      k_hop_round_generic<<<sm_count() * 8, 256, 0, s>>>(d.off, d.adj, d.labels, score, prev,
+                                                         d.n, d.L,
+                                                         idx + (int64_t)(h - 1) * d.n * d.L);
+    }
+  NURI_CUDA(cudaGetLastError());
+}
+
+// weight-ranked (or degree-ranked) label segments
+void build_label_segments(const DevGraph& d, const uint64_t* ckeys, const int32_t* score,
+                          DBuf<int2>& seg, DBuf<int64_t>* lsoff, cudaStream_t s) {
+  const int64_t nnz = d.nnz;
+  DBuf<uint64_t> k1, v1, k2, v2;
+  k1.alloc(nnz, s);
+  v1.alloc(nnz, s);
+  k2.alloc(nnz, s);
+  v2.alloc(nnz, s);
+  k_seg_keys<<<blocks_for(nnz), kThreads, 0, s>>>(ckeys, nnz, score, k1.p, v1.p);
+  size_t tmp_bytes = 0;
+  cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, k1.p, k2.p, v1.p, v2.p, nnz, 0, 64, s);
+  DBuf<uint8_t> tmp;
+  tmp.alloc(tmp_bytes, s);
+  NURI_CUDA(cub::DeviceRadixSort::SortPairs(tmp.p, tmp_bytes, k1.p, k2.p, v1.p, v2.p, nnz, 0,
+                                            64, s));
+  // v2 now in (score desc, id asc) order; stable sort by (row, label)
+  k_seg_primary<<<blocks_for(nnz), kThreads, 0, s>>>(v2.p, nnz, d.labels, d.L, k1.p);
+  int end_bit = bitlen((uint64_t)d.n * (uint64_t)d.L + 1);
+  size_t tmp2 = 0;
+  cub::DeviceRadixSort::SortPairs(nullptr, tmp2, k1.p, k2.p, v2.p, v1.p, nnz, 0, end_bit, s);
+  if (tmp2 > tmp_bytes) {
+    tmp.alloc(tmp2, s);
+    tmp_bytes = tmp2;
+  }
+  NURI_CUDA(cub::DeviceRadixSort::SortPairs(tmp.p, tmp_bytes, k1.p, k2.p, v2.p, v1.p, nnz, 0,
+                                            end_bit, s));
+  seg.alloc(nnz, s);
+  if (lsoff) {
+    int64_t nl = (int64_t)d.n * d.L;
+    DBuf<int32_t> cnt;
+    cnt.alloc(nl + 1, s);
+    NURI_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * (nl + 1), s));
+    k_seg_fill<<<blocks_for(nnz), kThreads, 0, s>>>(k2.p, v1.p, nnz, score, seg.p, cnt.p);
+    DBuf<int64_t> cnt64;
+    cnt64.alloc(nl + 1, s);
+    k_i32_to_i64<<<blocks_for(nl + 1), kThreads, 0, s>>>(cnt.p, nl + 1, cnt64.p);
+    lsoff->alloc(nl + 1, s);
+    size_t t3 = 0;
+    cub::DeviceScan::ExclusiveSum(nullptr, t3, cnt64.p, lsoff->p, nl + 1, s);
+    DBuf<uint8_t> tmp3;
+    tmp3.alloc(t3, s);
+    NURI_CUDA(cub::DeviceScan::ExclusiveSum(tmp3.p, t3, cnt64.p, lsoff->p, nl + 1, s));
+  } else {
+    DBuf<int32_t> dummy;
+    dummy.alloc((int64_t)d.n * d.L + 1, s);
+    NURI_CUDA(cudaMemsetAsync(dummy.p, 0, dummy.bytes(), s));
+    k_seg_fill<<<blocks_for(nnz), kThreads, 0, s>>>(k2.p, v1.p, nnz, score, seg.p, dummy.p);
+  }
+  NURI_CUDA(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------------------------
+void build_graph(nuri_graph* g, int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                 const uint8_t* labels, const int32_t* weights, int32_t index_hops,
+                 uint32_t flags, cudaStream_t s) {
+  const bool dev_in = flags & NURI_LOAD_DEVICE_INPUT;
+  DevGraph& d = g->d;
+  d.n = n;
+  // 1. inputs on the device
+  DBuf<int32_t> dsrc, ddst;
+  const int32_t *ps = src, *pd = dst;
+  if (!dev_in && m > 0) {
+    dsrc.alloc(m, s);
+    ddst.alloc(m, s);
+    NURI_CUDA(cudaMemcpyAsync(dsrc.p, src, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
+    NURI_CUDA(cudaMemcpyAsync(ddst.p, dst, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
+    ps = dsrc.p;
+    pd = ddst.p;
+  }
+  DBuf<int32_t> flag;
+  flag.alloc(4, s);
+  NURI_CUDA(cudaMemsetAsync(flag.p, 0, 16, s));
+  if (m > 0) k_validate<<<blocks_for(m), kThreads, 0, s>>>(ps, pd, m, n, flag.p);
+  int32_t bad = 0;
+  NURI_CUDA(cudaMemcpyAsync(&bad, flag.p, 4, cudaMemcpyDeviceToHost, s));
+  NURI_CUDA(cudaStreamSynchronize(s));
+  if (bad) NURI_FAIL(NURI_ERR_INVALID, "nuri_load_graph: vertex id outside [0, n)");
+
+  // 2. sorted, deduplicated directed keys
+  DBuf<uint64_t> keys, keys2;
+  int64_t two_m = 2 * m;
+  int64_t nnz = 0;
+  if (two_m > 0) {
+    keys.alloc(two_m, s);
+    keys2.alloc(two_m, s);
+    k_expand_pairs<<<blocks_for(m), kThreads, 0, s>>>(ps, pd, m, n, keys.p);
+    int end_bit = 32 + bitlen((uint64_t)n);
+    size_t tb = 0;
+    cub::DeviceRadixSort::SortKeys(nullptr, tb, keys.p, keys2.p, two_m, 0, end_bit, s);
+    DBuf<uint8_t> tmp;
+    tmp.alloc(tb, s);
+    NURI_CUDA(cub::DeviceRadixSort::SortKeys(tmp.p, tb, keys.p, keys2.p, two_m, 0, end_bit, s));
+    DBuf<int64_t> nsel;
+    nsel.alloc(1, s);
+    size_t tu = 0;
+    cub::DeviceSelect::Unique(nullptr, tu, keys2.p, keys.p, nsel.p, two_m, s);
+    if (tu > tb) tmp.alloc(tu, s);
+    NURI_CUDA(cub::DeviceSelect::Unique(tmp.p, tu, keys2.p, keys.p, nsel.p, two_m, s));
+    int64_t nuniq = 0;
+    uint64_t last = 0;
+    NURI_CUDA(cudaMemcpyAsync(&nuniq, nsel.p, 8, cudaMemcpyDeviceToHost, s));
+    NURI_CUDA(cudaStreamSynchronize(s));
+    if (nuniq > 0) {
+      NURI_CUDA(cudaMemcpyAsync(&last, keys.p + nuniq - 1, 8, cudaMemcpyDeviceToHost, s));
+      NURI_CUDA(cudaStreamSynchronize(s));
+    }
+    nnz = nuniq - ((nuniq > 0 && (last >> 32) == (uint64_t)(uint32_t)n) ? 1 : 0);
+  }
+  if (nnz >= ((int64_t)1 << 40)) NURI_FAIL(NURI_ERR_LIMIT, "graph too large");
+  d.nnz = nnz;
+  g->num_edges = nnz / 2;
+  g->dropped = m - nnz / 2;
+
+  // CSR
+  g->adj.alloc(nnz > 0 ? nnz : 1, s);
+  g->deg.alloc(n > 0 ? n : 1, s);
+  g->off.alloc((int64_t)n + 1, s);
+  NURI_CUDA(cudaMemsetAsync(g->deg.p, 0, sizeof(int32_t) * (n > 0 ? n : 1), s));
+  if (nnz > 0) k_split_keys<<<blocks_for(nnz), kThreads, 0, s>>>(keys.p, nnz, g->adj.p, g->deg.p);
+  {
+    DBuf<int64_t> deg64;
+    deg64.alloc((int64_t)n + 1, s);
+    NURI_CUDA(cudaMemsetAsync(deg64.p, 0, sizeof(int64_t) * (n + 1), s));
+    if (n > 0) k_i32_to_i64<<<blocks_for(n), kThreads, 0, s>>>(g->deg.p, n, deg64.p);
+    size_t t = 0;
+    cub::DeviceScan::ExclusiveSum(nullptr, t, deg64.p, g->off.p, (int64_t)n + 1, s);
+    DBuf<uint8_t> tmp;
+    tmp.alloc(t, s);
+    NURI_CUDA(cub::DeviceScan::ExclusiveSum(tmp.p, t, deg64.p, g->off.p, (int64_t)n + 1, s));
+  }
+  d.off = g->off.p;
+  d.adj = g->adj.p;
+  d.deg = g->deg.p;
+  {
+    DBuf<int32_t> mx;
+    mx.alloc(1, s);
+    NURI_CUDA(cudaMemsetAsync(mx.p, 0, 4, s));
+    if (n > 0) k_max_i32<<<blocks_for(n), kThreads, 0, s>>>(g->deg.p, n, mx.p);
+    NURI_CUDA(cudaMemcpyAsync(&d.max_deg, mx.p, 4, cudaMemcpyDeviceToHost, s));
+  }
+
+  // 3. degree orientation (rank space)
+  g->vert_of.alloc(n > 0 ? n : 1, s);
+  g->rank_of.alloc(n > 0 ? n : 1, s);
+  g->ooff.alloc((int64_t)n + 1, s);
+  int64_t half = nnz / 2;
+  g->oout.alloc(half > 0 ? half : 1, s);
+  if (n > 0) {
+    DBuf<uint64_t> rk, rk2;
+    rk.alloc(n, s);
+    rk2.alloc(n, s);
+    k_rank_keys<<<blocks_for(n), kThreads, 0, s>>>(g->deg.p, n, rk.p);
+    size_t t = 0;
+    cub::DeviceRadixSort::SortKeys(nullptr, t, rk.p, rk2.p, n, 0, 64, s);
+    DBuf<uint8_t> tmp;
+    tmp.alloc(t, s);
+    NURI_CUDA(cub::DeviceRadixSort::SortKeys(tmp.p, t, rk.p, rk2.p, n, 0, 64, s));
+    k_rank_split<<<blocks_for(n), kThreads, 0, s>>>(rk2.p, n, g->vert_of.p, g->rank_of.p);
+  }
+  DBuf<int32_t> odeg;
+  odeg.alloc((int64_t)n + 1, s);
+  NURI_CUDA(cudaMemsetAsync(odeg.p, 0, sizeof(int32_t) * (n + 1), s));
+  if (nnz > 0) {
+    k_orient_keys<<<blocks_for(nnz), kThreads, 0, s>>>(keys.p, nnz, g->rank_of.p, n, keys2.p);
+    int end_bit = 32 + bitlen((uint64_t)n);
+    DBuf<uint64_t> ok2;
+    ok2.alloc(nnz, s);
+    size_t t = 0;
+    cub::DeviceRadixSort::SortKeys(nullptr, t, keys2.p, ok2.p, nnz, 0, end_bit, s);
+    DBuf<uint8_t> tmp;
+    tmp.alloc(t, s);
+    NURI_CUDA(cub::DeviceRadixSort::SortKeys(tmp.p, t, keys2.p, ok2.p, nnz, 0, end_bit, s));
+    k_orient_split<<<blocks_for(half), kThreads, 0, s>>>(ok2.p, half, g->oout.p, odeg.p);
+  }
+  {
+    DBuf<int64_t> od64;
+    od64.alloc((int64_t)n + 1, s);
+    NURI_CUDA(cudaMemsetAsync(od64.p, 0, sizeof(int64_t) * (n + 1), s));
+    if (n > 0) k_i32_to_i64<<<blocks_for(n), kThreads, 0, s>>>(odeg.p, n, od64.p);
+    size_t t = 0;
+    cub::DeviceScan::ExclusiveSum(nullptr, t, od64.p, g->ooff.p, (int64_t)n + 1, s);
+    DBuf<uint8_t> tmp;
+    tmp.alloc(t, s);
+    NURI_CUDA(cub::DeviceScan::ExclusiveSum(tmp.p, t, od64.p, g->ooff.p, (int64_t)n + 1, s));
+    DBuf<int32_t> mx;
+    mx.alloc(1, s);
+    NURI_CUDA(cudaMemsetAsync(mx.p, 0, 4, s));
+    if (n > 0) k_max_i32<<<blocks_for(n), kThreads, 0, s>>>(odeg.p, n, mx.p);
+    NURI_CUDA(cudaMemcpyAsync(&d.max_out, mx.p, 4, cudaMemcpyDeviceToHost, s));
+  }
+  d.ooff = g->ooff.p;
+  d.oout = g->oout.p;
+  d.vert_of = g->vert_of.p;
+  d.rank_of = g->rank_of.p;
+
+  // 4. labels, weights, label segments, hop index
+  if (weights) {
+    g->weights.alloc(n > 0 ? n : 1, s);
+    if (n > 0)
+      NURI_CUDA(cudaMemcpyAsync(g->weights.p, weights, sizeof(int32_t) * n,
+                                dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    d.weights = g->weights.p;
+    DBuf<int32_t> mn;
+    mn.alloc(1, s);
+    int32_t init = INT32_MAX;
+    NURI_CUDA(cudaMemcpyAsync(mn.p, &init, 4, cudaMemcpyHostToDevice, s));
+    if (n > 0) k_min_i32<<<blocks_for(n), kThreads, 0, s>>>(g->weights.p, n, mn.p);
+    int32_t wmin = 0;
+    NURI_CUDA(cudaMemcpyAsync(&wmin, mn.p, 4, cudaMemcpyDeviceToHost, s));
+    NURI_CUDA(cudaStreamSynchronize(s));
+    if (n > 0 && wmin < 0) NURI_FAIL(NURI_ERR_INVALID, "nuri_load_graph: negative weight");
+  }
+  if (labels) {
+    g->labels.alloc(n > 0 ? n : 1, s);
+    if (n > 0)
+      NURI_CUDA(cudaMemcpyAsync(g->labels.p, labels, n,
+                                dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    d.labels = g->labels.p;
+    DBuf<int32_t> mx;
+    mx.alloc(1, s);
+    NURI_CUDA(cudaMemsetAsync(mx.p, 0, 4, s));
+    if (n > 0) k_max_u8<<<blocks_for(n), kThreads, 0, s>>>(g->labels.p, n, mx.p);
+    int32_t lmax = 0;
+    NURI_CUDA(cudaMemcpyAsync(&lmax, mx.p, 4, cudaMemcpyDeviceToHost, s));
+    NURI_CUDA(cudaStreamSynchronize(s));
+    d.L = lmax + 1;
+  }
+  NURI_CUDA(cudaStreamSynchronize(s));
+  if (labels && !(flags & NURI_LOAD_NO_ISO) && n > 0) {
+    // degree-ranked segments always (patterns and degree-sum isomorphism use them)
+    build_label_segments(d, keys.p, g->deg.p, g->lseg_d, &g->lsoff, s);
+    d.lsoff = g->lsoff.p;
+    d.lseg_d = g->lseg_d.p;
+    g->gmax_d.alloc(d.L, s);
+    NURI_CUDA(cudaMemsetAsync(g->gmax_d.p, 0xff, sizeof(int32_t) * d.L, s));
+    k_gmax<<<blocks_for(n), kThreads, 0, s>>>(g->labels.p, g->deg.p, n, g->gmax_d.p);
+    d.gmax_d = g->gmax_d.p;
+    if (weights) {
+      build_label_segments(d, keys.p, g->weights.p, g->lseg_w, nullptr, s);
+      d.lseg_w = g->lseg_w.p;
+      g->gmax_w.alloc(d.L, s);
+      NURI_CUDA(cudaMemsetAsync(g->gmax_w.p, 0xff, sizeof(int32_t) * d.L, s));
+      k_gmax<<<blocks_for(n), kThreads, 0, s>>>(g->labels.p, g->weights.p, n, g->gmax_w.p);
+      d.gmax_w = g->gmax_w.p;
+    }
+    if (index_hops > 0) {
+      d.H = index_hops;
+      if (weights) {
+        g->idx_w.alloc((int64_t)index_hops * n * d.L, s);
+        build_hop_index(d, g->weights.p, index_hops, g->idx_w.p, s);
+        d.idx_w = g->idx_w.p;
+      }
+      g->idx_d.alloc((int64_t)index_hops * n * d.L, s);
+      build_hop_index(d, g->deg.p, index_hops, g->idx_d.p, s);
+      d.idx_d = g->idx_d.p;
+    }
+  }
+  NURI_CUDA(cudaGetLastError());
+  NURI_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace nuri

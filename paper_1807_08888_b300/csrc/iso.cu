@@ -1,0 +1,7 @@
+#include "nuri_internal.cuh"
+namespace nuri {
+void topk_iso_batch(nuri_graph*, int32_t, const nuri_query*, const int32_t*, int32_t, uint32_t,
+                    cudaStream_t, nuri_result**) {
+  NURI_FAIL(NURI_ERR_INVALID, "isomorphism queries are not available in this build");
+}
+}  // namespace nuri

@@ -1,0 +1,187 @@
+// Internal declarations shared by the translation units of libnuri.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "nuri.h"
+
+namespace nuri {
+
+// ------------------------------------------------------------------------------------------
+// errors
+// ------------------------------------------------------------------------------------------
+void set_error(const char* fmt, ...);
+const char* last_error();
+
+struct Err {
+  nuri_status code;
+};
+
+// Throws Err on a CUDA failure; every C entry point catches and converts to a status.
+#define NURI_CUDA(call)                                                                    \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) {                                                              \
+      ::nuri::set_error("CUDA error %s at %s:%d: %s", cudaGetErrorName(e_), __FILE__,     \
+                        __LINE__, cudaGetErrorString(e_));                                \
+      throw ::nuri::Err{e_ == cudaErrorMemoryAllocation ? NURI_ERR_OOM : NURI_ERR_CUDA};  \
+    }                                                                                     \
+  } while (0)
+
+#define NURI_FAIL(code, ...)          \
+  do {                                \
+    ::nuri::set_error(__VA_ARGS__);   \
+    throw ::nuri::Err{code};          \
+  } while (0)
+
+// ------------------------------------------------------------------------------------------
+// stream-ordered device buffers
+// ------------------------------------------------------------------------------------------
+template <class T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  cudaStream_t s = nullptr;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept { swap(o); }
+  DBuf& operator=(DBuf&& o) noexcept {
+    reset();
+    swap(o);
+    return *this;
+  }
+  ~DBuf() { reset(); }
+  void swap(DBuf& o) {
+    std::swap(p, o.p);
+    std::swap(n, o.n);
+    std::swap(s, o.s);
+  }
+  void alloc(size_t count, cudaStream_t st) {
+    reset();
+    s = st;
+    n = count;
+    if (count) NURI_CUDA(cudaMallocAsync((void**)&p, sizeof(T) * count, st));
+  }
+  void reset() {
+    if (p) cudaFreeAsync(p, s);
+    p = nullptr;
+    n = 0;
+  }
+  size_t bytes() const { return sizeof(T) * n; }
+};
+
+// ------------------------------------------------------------------------------------------
+// the device-resident graph
+// ------------------------------------------------------------------------------------------
+// Layouts (all int32 vertex ids, int64 row offsets):
+//   adj      : undirected CSR, each row sorted by id                  off[n+1], adj[2|E|]
+//   orientation for cliques: rank(v) = position of v in (degree, id) ascending order;
+//     oout   : out-rows in rank space, row r = ranks of neighbours with larger rank, sorted
+//     vert_of: rank -> original id
+//   label segments for isomorphism / patterns: the row of v is grouped by neighbour label;
+//     segment (v, l) = lseg[lsoff[v*L + l] .. lsoff[v*L + l + 1]) holds {id, score} pairs
+//     sorted by score descending, then id ascending (weight-ranked candidate lists)
+//   hop index: idx[((h-1) * n + v) * L + l], h = 1..H (cumulative walk reachability)
+struct DevGraph {
+  int32_t n = 0;
+  int64_t nnz = 0;        // directed entries = 2|E|
+  int32_t L = 0;          // number of labels (0 = unlabelled)
+  int32_t max_deg = 0, max_out = 0;
+  const int64_t* off = nullptr;
+  const int32_t* adj = nullptr;
+  const int32_t* deg = nullptr;
+  const int64_t* ooff = nullptr;
+  const int32_t* oout = nullptr;
+  const int32_t* vert_of = nullptr;
+  const int32_t* rank_of = nullptr;
+  const uint8_t* labels = nullptr;
+  const int32_t* weights = nullptr;
+  const int64_t* lsoff = nullptr;   // [n*L + 1]
+  const int2* lseg_w = nullptr;     // weight-ranked segments {id, weight}
+  const int2* lseg_d = nullptr;     // degree-ranked segments {id, degree}
+  const int32_t* idx_w = nullptr;   // hop index over weights
+  const int32_t* idx_d = nullptr;   // hop index over degrees
+  const int32_t* gmax_w = nullptr;  // [L] global per-label max weight
+  const int32_t* gmax_d = nullptr;  // [L] global per-label max degree
+  int32_t H = 0;
+};
+
+}  // namespace nuri
+
+struct nuri_graph {
+  nuri::DevGraph d;
+  int64_t num_edges = 0, dropped = 0;
+  cudaStream_t stream = nullptr;
+  nuri::DBuf<int64_t> off, ooff, lsoff;
+  nuri::DBuf<int32_t> adj, deg, oout, vert_of, rank_of, weights, idx_w, idx_d, gmax_w, gmax_d;
+  nuri::DBuf<uint8_t> labels;
+  nuri::DBuf<int2> lseg_w, lseg_d;
+  std::vector<int32_t> h_deg_sorted_bounds;  // unused placeholder for host-side caches
+  int64_t device_bytes() const {
+    return off.bytes() + ooff.bytes() + lsoff.bytes() + adj.bytes() + deg.bytes() +
+           oout.bytes() + vert_of.bytes() + rank_of.bytes() + weights.bytes() + idx_w.bytes() +
+           idx_d.bytes() + gmax_w.bytes() + gmax_d.bytes() + labels.bytes() + lseg_w.bytes() +
+           lseg_d.bytes();
+  }
+};
+
+namespace nuri {
+
+// graph_build.cu
+void build_graph(nuri_graph* g, int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                 const uint8_t* labels, const int32_t* weights, int32_t index_hops,
+                 uint32_t flags, cudaStream_t s);
+
+// result packing (capi.cu)
+nuri_result* new_result(int kind, int32_t count, int64_t nverts, int64_t nedges, bool labels);
+
+// cliques.cu
+void topk_cliques(nuri_graph* g, int32_t k, uint32_t flags, int64_t frontier_cap,
+                  cudaStream_t s, nuri_result** out);
+
+// iso.cu
+void topk_iso_batch(nuri_graph* g, int32_t nq, const nuri_query* qs, const int32_t* ks,
+                    int32_t rank, uint32_t flags, cudaStream_t s, nuri_result** outs);
+
+// patterns.cu
+void topk_patterns(nuri_graph* g, int32_t M, int32_t k, uint32_t flags, cudaStream_t s,
+                   nuri_result** out);
+
+// timing helper: device events on the query stream
+struct DevTimer {
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaStream_t s;
+  explicit DevTimer(cudaStream_t st) : s(st) {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, s);
+  }
+  double stop() {
+    cudaEventRecord(b, s);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms;
+  }
+  ~DevTimer() {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+};
+
+inline int sm_count() {
+  static int c = 0;
+  if (!c) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
+    if (c <= 0) c = 148;
+  }
+  return c;
+}
+
+}  // namespace nuri

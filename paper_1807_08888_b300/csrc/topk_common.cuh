@@ -1,0 +1,32 @@
+// Device helpers shared by the query engines: the global k-th-best threshold and result
+// appends (Algorithm 1 lines 6-10 and the dominated() test of lines 11 and 15).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace nuri {
+
+__device__ __forceinline__ int32_t ld_volatile(const int32_t* p) {
+  return *(const volatile int32_t*)p;
+}
+
+// Threshold from a score histogram: tau = max t with sum_{s >= t} hist[s] >= k, or INT32_MIN
+// when fewer than k results exist.  Bins may be coarse (score >> shift): the value returned
+// is then the lower edge of the bin, still a valid lower bound of the exact k-th score.
+// Any snapshot of the counters undercounts the final histogram, so every value computed
+// here is <= the final k-th score; publishing it with atomicMax keeps tau monotone.
+__device__ __forceinline__ void publish_threshold(const int32_t* hist, int32_t nbins,
+                                                  int32_t shift, int64_t k, int32_t* tau) {
+  int64_t acc = 0;
+  for (int32_t b = nbins - 1; b >= 0; --b) {
+    acc += ld_volatile(hist + b);
+    if (acc >= k) {
+      int32_t t = b << shift;
+      if (t > ld_volatile(tau)) atomicMax(tau, t);
+      return;
+    }
+  }
+}
+
+}  // namespace nuri
