@@ -43,7 +43,7 @@ typedef int32_t nuri_status;
 #define NURI_ERR_INVALID 1   /* bad argument: k < 1, id out of range, bad query, ...      */
 #define NURI_ERR_OOM 2       /* device or pinned-host allocation failed                    */
 #define NURI_ERR_LIMIT 3     /* a built-in size limit was exceeded (clique size > 128, ...) */
-#define NURI_ERR_TIMEOUT 4   /* a bounded device wait ran out                              */
+#define NURI_ERR_TIMEOUT 4   /* the query ran past its time budget (nuri_set_time_budget)  */
 #define NURI_ERR_CANCELLED 5 /* the request was cancelled                                  */
 #define NURI_ERR_CUDA 6      /* a CUDA runtime call failed                                 */
 
@@ -195,6 +195,14 @@ nuri_status nuri_topk_patterns(nuri_graph* g, int32_t M, int32_t k, int32_t rank
  */
 nuri_status nuri_hop_index(nuri_graph* g, int32_t hops, int32_t degree_rank, int32_t* out,
                            int32_t device_out, void* stream);
+
+/*
+ * nuri_set_time_budget -- limit the device time of every later query on any graph: a query
+ * whose kernels run past `ms` milliseconds stops and returns NURI_ERR_TIMEOUT (the graph
+ * stays usable).  The check reads the GPU's global timer inside the search loops; no kernel
+ * waits on anything.  0 (the default) means no limit.  Process-wide setting.
+ */
+nuri_status nuri_set_time_budget(double ms);
 
 void nuri_free_result(nuri_result* r);
 

@@ -20,7 +20,7 @@ import numpy as np
 
 __all__ = [
     "NuriError", "lib", "load_graph", "Graph", "topk_cliques", "topk_iso", "topk_iso_batch",
-    "topk_patterns", "hop_index", "Result", "LIB_PATH", "EXPORTS",
+    "topk_patterns", "hop_index", "set_time_budget", "Result", "LIB_PATH", "EXPORTS",
     "RANK_SIZE", "RANK_WEIGHT_SUM", "RANK_DEGREE_SUM", "RANK_MNI",
 ]
 
@@ -37,7 +37,7 @@ KEEP_TIES, NO_PRUNE = 0x100, 0x200
 EXPORTS = (
     "nuri_load_graph", "nuri_free_graph", "nuri_graph_get_info", "nuri_topk_cliques",
     "nuri_topk_iso", "nuri_topk_iso_batch", "nuri_topk_patterns", "nuri_hop_index",
-    "nuri_free_result", "nuri_last_error", "nuri_version",
+    "nuri_free_result", "nuri_last_error", "nuri_version", "nuri_set_time_budget",
 )
 
 
@@ -119,6 +119,8 @@ def lib():
             L.nuri_topk_patterns.restype = i32
             L.nuri_hop_index.argtypes = [P, i32, i32, P, i32, P]
             L.nuri_hop_index.restype = i32
+            L.nuri_set_time_budget.argtypes = [ctypes.c_double]
+            L.nuri_set_time_budget.restype = i32
             L.nuri_free_result.argtypes = [ctypes.POINTER(_Result)]
             L.nuri_free_result.restype = None
             L.nuri_last_error.restype = ctypes.c_char_p
@@ -291,6 +293,12 @@ def hop_index(g: Graph, hops: int, degree_rank=False, stream=None) -> np.ndarray
     _check(lib().nuri_hop_index(g.handle, int(hops), int(bool(degree_rank)),
                                 out.ctypes.data_as(ctypes.c_void_p), 0, _stream(stream)))
     return out
+
+
+def set_time_budget(ms: float) -> None:
+    """Limit the device time of every later query (0 = no limit); overruns raise NuriError
+    with code ERR_TIMEOUT."""
+    _check(lib().nuri_set_time_budget(float(ms)))
 
 
 def version() -> str:

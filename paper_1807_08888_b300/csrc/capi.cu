@@ -1,5 +1,6 @@
 // C ABI of libnuri (declared in include/nuri.h): argument checks, error conversion, result
 // allocation.  Every entry point catches the library's internal errors and returns a status.
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -20,6 +21,14 @@ void set_error(const char* fmt, ...) {
 }
 
 const char* last_error() { return g_err; }
+
+static std::atomic<uint64_t> g_budget_ns{0};
+uint64_t time_budget_ns() { return g_budget_ns.load(); }
+
+__global__ void k_set_deadline(uint64_t* deadline, uint64_t budget_ns) {
+  if (threadIdx.x == 0 && blockIdx.x == 0)
+    *deadline = budget_ns ? global_ns() + budget_ns : ~0ull;
+}
 
 nuri_result* new_result(int kind, int32_t count, int64_t nverts, int64_t nedges, bool labels) {
   nuri_result* r = (nuri_result*)calloc(1, sizeof(nuri_result));
@@ -162,6 +171,13 @@ nuri_status nuri_topk_patterns(nuri_graph* g, int32_t M, int32_t k, int32_t rank
     if (rank != NURI_RANK_MNI) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_patterns: rank must be NURI_RANK_MNI");
     if (!g->d.labels || !g->d.lsoff) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_patterns: graph has no labels");
     topk_patterns(g, M, k, flags, (cudaStream_t)stream, out);
+  });
+}
+
+nuri_status nuri_set_time_budget(double ms) {
+  return guarded([&] {
+    if (!(ms >= 0.0)) NURI_FAIL(NURI_ERR_INVALID, "nuri_set_time_budget: ms must be >= 0");
+    g_budget_ns.store((uint64_t)(ms * 1e6));
   });
 }
 

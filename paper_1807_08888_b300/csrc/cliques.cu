@@ -6,12 +6,14 @@
 //                here the order is the degree orientation rank (any total order enumerates
 //                every clique exactly once; results are reported in original ids)
 //   expandable = d in P_s;  relevant = true (all cliques) or maximality (flag)
-//   bound      = |V_s| + |P_s| (Carraghan-Pardalos);  prune iff bound < tau (strict)
+//   bound      = |V_s| + |P_s| (Carraghan-Pardalos), tightened inside the bitmap tail to
+//                |V_s| + (colours of a greedy colouring of P_s); prune iff bound < tau (strict)
 //   tau        = k-th best size among results found so far (global, atomicMax, monotone)
 //
 // Work is organised as a bucketed best-first frontier driven from the host:
 //   * seeds (one per vertex, Alg.1 lines 1-3) are sorted by bound and consumed in
-//     descending-bound chunks; frontier records live in 64 buckets keyed by bound;
+//     descending-bound chunks; frontier records live in 256 buckets keyed by bound (LIFO
+//     inside a bucket, so the deepest records of the best bound go first);
 //   * each round takes the highest bucket (or seed chunk) whose bound >= tau and expands it
 //     with one warp per record (k_clique_expand);
 //   * a record with |P| <= 64 is finished in place: the warp builds the 64x64 bit adjacency
@@ -42,7 +44,8 @@ namespace {
 
 constexpr int MAXD = 128;      // largest clique the records can hold
 constexpr int BM = 64;         // bitmap tail handles |P| <= BM
-constexpr int NB = 64;         // frontier buckets (bucket NB-1 holds every bound >= NB-1)
+constexpr int NB = 256;        // frontier buckets (bucket NB-1 holds every bound >= NB-1;
+                               // cliques never exceed MAXD < NB-1, so the order is exact)
 constexpr int WARPS = 4;       // warps per CTA of the expansion kernel
 constexpr int PSMEM = 512;     // P entries staged in shared memory per warp
 
@@ -54,12 +57,13 @@ struct Rec {
 
 struct QState {
   int32_t tau;
-  int32_t err;           // bit 0: clique larger than MAXD
+  int32_t err;           // bit 0: clique larger than MAXD; bit 2: time budget exhausted
   int64_t res_count;     // results appended (may exceed the capacity: then a re-run)
   int64_t stage_count;   // children slots reserved in the staging array
   int64_t defer_count;   // parents sent back because the staging array was full
   int64_t work_next;     // dynamic work counter
   unsigned long long expansions, pruned, dequeued, adj_bytes;
+  int32_t hmax;          // largest clique size recorded so far
   int32_t hist[MAXD + 2];
 };
 
@@ -130,7 +134,12 @@ struct Ctx {
   int32_t k;
   int32_t maximal;
   int32_t no_prune;
+  const uint64_t* deadline;  // global timer value after which the query stops (err bit 2)
 };
+
+__device__ __forceinline__ bool past_deadline(const Ctx& cx) {
+  return global_ns() > *(const volatile uint64_t*)cx.deadline;
+}
 
 // Append one clique (ranks) of size c as a candidate result and refresh tau.
 __device__ void add_result(const Ctx& cx, const int32_t* V, int nv, int32_t extra_count,
@@ -145,7 +154,9 @@ __device__ void add_result(const Ctx& cx, const int32_t* V, int nv, int32_t extr
     for (int i = 0; i < extra_count; ++i) r->V[nv + i] = extra[i];
   }
   atomicAdd(&cx.st->hist[c], 1);
-  publish_threshold(cx.st->hist, MAXD + 1, 0, cx.k, &cx.st->tau);
+  if (c > ld_volatile(&cx.st->hmax)) atomicMax(&cx.st->hmax, c);
+  if ((int64_t)(slot + 1) < (int64_t)cx.k) return;  // fewer than k results so far
+  publish_threshold(cx.st->hist, ld_volatile(&cx.st->hmax), 0, cx.k, &cx.st->tau);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -157,7 +168,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_clique_expand(Ctx cx, const Rec*
                                                               const int32_t* __restrict__ seeds,
                                                               int64_t nin) {
   __shared__ int32_t sP[WARPS][PSMEM];
-  __shared__ unsigned long long sRow[WARPS][BM];
+  __shared__ unsigned long long sRow[WARPS][BM];   // neighbours with a larger index in P
+  __shared__ unsigned long long sFull[WARPS][BM];  // all neighbours inside P
   __shared__ int32_t sV[WARPS][MAXD];
 
   const int lane = threadIdx.x & 31;
@@ -172,7 +184,13 @@ __global__ void __launch_bounds__(WARPS * 32) k_clique_expand(Ctx cx, const Rec*
   while (true) {
     int64_t item = 0;
     __syncwarp();  // every lane is done with the previous record's shared state
-    if (lane == 0) item = (int64_t)atomicAdd((unsigned long long*)&cx.st->work_next, 1ull);
+    if (lane == 0) {
+      item = (int64_t)atomicAdd((unsigned long long*)&cx.st->work_next, 1ull);
+      if (item < nin && past_deadline(cx)) {
+        atomicOr(&cx.st->err, 4);
+        item = nin;
+      }
+    }
     item = __shfl_sync(FULL, item, 0);
     if (item >= nin) break;
 
@@ -311,23 +329,93 @@ __global__ void __launch_bounds__(WARPS * 32) k_clique_expand(Ctx cx, const Rec*
         }
       }
       __syncwarp();
+      // symmetric rows for the colouring bound
+      for (int j = lane; j < p; j += 32) {
+        unsigned long long f = sRow[w][j];
+        for (int i = 0; i < j; ++i) f |= ((sRow[w][i] >> j) & 1ull) << i;
+        sFull[w][j] = f;
+      }
+      __syncwarp();
       // lane-parallel depth-first search: lane owns the children j = lane, lane + 32.
       // Per-lane stack (local memory): stk[d] = untried candidates of the node at depth d,
       // pick[d] = index in P of the vertex added at depth d (depth <= |P| <= 64).
       bool limit_hit = false;
       unsigned long long stk[BM];
       uint8_t pick[BM + 1];
-      for (int j = lane; j < p; j += 32) {
-        int depth = 0;  // picks below the record minus one
-        pick[0] = (uint8_t)j;
-        unsigned long long X = sRow[w][j];
+      // Lane tasks: task j < p is the child node {P_j} alone; the other tasks are the
+      // subtrees rooted at the grandchildren {P_j, P_b} (b in row[j]), so a dense child's
+      // subtree is spread over many lanes.  Every node is visited by exactly one task.
+      int ntask = p;
+      for (int j = 0; j < p; ++j) ntask += __popcll(sRow[w][j]);
+      bool out_of_time = false;
+      int32_t t_cache = ld_volatile(&cx.st->tau);
+      int tj = 0, tb = -1;  // (j, b) of the task with index tnext
+      int tnext = 0;
+      for (int task = lane; task < ntask && !out_of_time; task += 32) {
+        int depth;
+        unsigned long long X;
+        if (task < p) {
+          depth = 0;
+          pick[0] = (uint8_t)task;
+          X = sRow[w][task];
+        } else {
+          // walk the (j, b) enumeration forward to index `task`
+          if (tnext < p) {
+            tnext = p;
+            tj = 0;
+            while (sRow[w][tj] == 0) ++tj;
+            tb = __ffsll((long long)sRow[w][tj]) - 1;
+          }
+          while (tnext < task) {
+            unsigned long long rest = tb >= 63 ? 0ull : (sRow[w][tj] & ~((2ull << tb) - 1));
+            if (rest) {
+              tb = __ffsll((long long)rest) - 1;
+            } else {
+              do {
+                ++tj;
+              } while (sRow[w][tj] == 0);
+              tb = __ffsll((long long)sRow[w][tj]) - 1;
+            }
+            ++tnext;
+          }
+          depth = 1;
+          pick[0] = (uint8_t)tj;
+          pick[1] = (uint8_t)tb;
+          X = sRow[w][tj] & sRow[w][tb];
+          stk[0] = 0;  // the siblings of this grandchild are other tasks
+        }
+        const bool single = task < p;  // a child task visits its own node only
         while (true) {
           // node: record + pick[0..depth], candidates X
           int size = nv + depth + 1;
           ++my_exp;
-          int32_t t_now = ld_volatile(&cx.st->tau);
+          if ((my_exp & 31) == 0) {
+            t_cache = ld_volatile(&cx.st->tau);
+            if ((my_exp & 1023) == 0 && past_deadline(cx)) {
+              atomicOr(&cx.st->err, 4);
+              out_of_time = true;
+              break;
+            }
+          }
+          int32_t t_now = t_cache;
           int bnd = size + __popcll(X);
-          bool expand_node = true;
+          // a greedy colouring of the candidates bounds the clique they can add (a clique
+          // takes at most one vertex per colour class); tighter than |P| on dense candidates
+          if (!cx.no_prune && bnd >= t_now && X != 0 && bnd - 1 > size) {
+            int colours = 0;
+            unsigned long long left = X;
+            while (left) {
+              ++colours;
+              unsigned long long cls = left;
+              while (cls) {
+                int v = __ffsll((long long)cls) - 1;
+                cls &= ~sFull[w][v] & ~(1ull << v);
+                left &= ~(1ull << v);
+              }
+            }
+            bnd = size + colours;
+          }
+          bool expand_node = !single;
           if (!cx.no_prune && bnd < t_now) {
             ++my_pruned;
             expand_node = false;
@@ -344,7 +432,10 @@ __global__ void __launch_bounds__(WARPS * 32) k_clique_expand(Ctx cx, const Rec*
                 rel = is_maximal(g, C, size);
               }
             }
-            if (rel) add_result(cx, sV[w], nv, depth + 1, pick_ranks);
+            if (rel) {
+              add_result(cx, sV[w], nv, depth + 1, pick_ranks);
+              t_cache = ld_volatile(&cx.st->tau);
+            }
           }
           if (expand_node && X != 0 && size >= MAXD) {
             limit_hit = true;
@@ -360,17 +451,17 @@ __global__ void __launch_bounds__(WARPS * 32) k_clique_expand(Ctx cx, const Rec*
             X = rest & sRow[w][b];
             continue;
           }
-          // back up to the next sibling that can still reach tau
+          if (single) break;
+          // back up to the next sibling that can still reach tau (depth 1 is the task root)
           bool done = false;
           while (true) {
-            if (depth == 0) {
+            if (depth <= 1) {
               done = true;
               break;
             }
             unsigned long long rest = stk[depth - 1];
             int parent_size = nv + depth;  // size of the node whose children are iterated
-            int32_t t2 = ld_volatile(&cx.st->tau);
-            if (rest == 0 || (!cx.no_prune && parent_size + __popcll(rest) < t2)) {
+            if (rest == 0 || (!cx.no_prune && parent_size + __popcll(rest) < t_cache)) {
               --depth;
               continue;
             }
@@ -601,6 +692,10 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
 
   DBuf<QState> st;
   st.alloc(1, s);
+  DBuf<uint64_t> deadline;
+  deadline.alloc(1, s);
+  ++launches;
+  k_set_deadline<<<1, 32, 0, s>>>(deadline.p, time_budget_ns());
   DBuf<int32_t> pscratch;
   if (g.max_out > PSMEM) pscratch.alloc((int64_t)total_warps * g.max_out, s);
   DBuf<Rec> stage, deferred, inbuf;
@@ -690,6 +785,7 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
     cx.k = k;
     cx.maximal = maximal;
     cx.no_prune = no_prune;
+    cx.deadline = deadline.p;
     int64_t rounds = 0;
     int64_t seed_chunk = std::max<int64_t>(total_warps, 1024);
 
@@ -697,6 +793,7 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
       NURI_CUDA(cudaMemcpyAsync(&hs, st.p, sizeof(hs), cudaMemcpyDeviceToHost, s));
       NURI_CUDA(cudaStreamSynchronize(s));
       if (hs.err & 1) NURI_FAIL(NURI_ERR_LIMIT, "nuri_topk_cliques: a clique exceeds %d vertices", MAXD);
+      if (hs.err & 4) NURI_FAIL(NURI_ERR_TIMEOUT, "nuri_topk_cliques: time budget exhausted after %lld rounds", (long long)rounds);
       int32_t tau = hs.tau;
       // highest bucket with pending seeds or records
       int b_seed = -1, b_front = -1;

@@ -4,8 +4,9 @@
 // Steps (all on the device, stream-ordered):
 //   1. validate ids, expand each input pair to both directions, drop self-loops
 //   2. radix-sort the 64-bit (row, col) keys, drop duplicates -> undirected CSR (sorted rows)
-//   3. degree orientation for cliques: rank = position in (degree, id) order; out-rows in rank
-//      space keep only neighbours of larger rank (bounded out-degree on power-law graphs)
+//   3. degeneracy orientation for cliques: rank = position in the batch-peeling order (core
+//      decomposition); out-rows in rank space keep only neighbours of larger rank, so every
+//      out-row has at most degeneracy(G) entries
 //   4. label segments: each row grouped by neighbour label, each group sorted by score desc
 //   5. hop/label max index, H rounds of a gather-max over neighbours
 #include <cub/cub.cuh>
@@ -79,6 +80,65 @@ __global__ void k_rank_split(const uint64_t* __restrict__ keys, int32_t n,
     vert_of[r] = v;
     rank_of[v] = (int32_t)r;
   }
+}
+
+// ---- degeneracy order by batch peeling -------------------------------------------------
+// A vertex is removed in the first batch where its remaining degree is <= k (k = the current
+// core level); at that moment at most k of its neighbours remain, so every vertex has at most
+// degeneracy(G) neighbours later in the (batch, id) order.
+__global__ void k_peel_init(const int32_t* __restrict__ deg, int32_t n, int32_t* __restrict__ rem,
+                            int32_t* __restrict__ batch) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    rem[v] = deg[v];
+    batch[v] = -1;
+  }
+}
+
+__global__ void k_peel_min(const int32_t* __restrict__ rem, const int32_t* __restrict__ batch,
+                           int32_t n, int32_t* out) {
+  int32_t best = INT32_MAX;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    if (batch[v] < 0) best = min(best, rem[v]);
+  for (int o = 16; o; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if ((threadIdx.x & 31) == 0) atomicMin(out, best);
+}
+
+__global__ void k_peel_select(const int32_t* __restrict__ rem, int32_t* __restrict__ batch,
+                              int32_t n, int32_t k, int32_t b, int32_t* __restrict__ front,
+                              int32_t* cnt) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    if (batch[v] < 0 && rem[v] <= k) {
+      batch[v] = b;
+      front[atomicAdd(cnt, 1)] = (int32_t)v;
+    }
+}
+
+__global__ void k_peel_remove(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+                              const int32_t* __restrict__ front, int32_t nfront, int32_t k,
+                              int32_t b, int32_t* __restrict__ rem, int32_t* __restrict__ batch,
+                              int32_t* __restrict__ next, int32_t* ncnt) {
+  // one warp per removed vertex
+  const int lane = threadIdx.x & 31;
+  for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < nfront;
+       w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    int32_t v = front[w];
+    for (int64_t t = off[v] + lane; t < off[v + 1]; t += 32) {
+      int32_t u = adj[t];
+      if (*(volatile int32_t*)(batch + u) >= 0) continue;
+      int32_t old = atomicSub(rem + u, 1);
+      if (old - 1 <= k && atomicCAS(batch + u, -1, b + 1) == -1) next[atomicAdd(ncnt, 1)] = u;
+    }
+  }
+}
+
+__global__ void k_peel_keys(const int32_t* __restrict__ batch, int32_t n,
+                            uint64_t* __restrict__ keys) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    keys[v] = ((uint64_t)(uint32_t)batch[v] << 32) | (uint32_t)v;
 }
 
 // one key per directed entry whose target has the larger rank; the rest become sentinels
@@ -171,6 +231,22 @@ __global__ void k_i32_to_i64(const int32_t* __restrict__ a, int64_t n, int64_t* 
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     b[i] = a[i];
+}
+
+__global__ void k_label_keys(const uint8_t* __restrict__ labels, int32_t n,
+                             uint64_t* __restrict__ keys) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    keys[i] = ((uint64_t)labels[i] << 32) | (uint32_t)i;
+}
+
+__global__ void k_label_split(const uint64_t* __restrict__ keys, int32_t n,
+                              int32_t* __restrict__ vert, int32_t* __restrict__ cnt) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    vert[i] = (int32_t)(uint32_t)keys[i];
+    atomicAdd(&cnt[keys[i] >> 32], 1);
+  }
 }
 
 __global__ void k_gmax(const uint8_t* __restrict__ labels, const int32_t* __restrict__ score,
@@ -385,6 +461,56 @@ void build_label_segments(const DevGraph& d, const uint64_t* ckeys, const int32_
   NURI_CUDA(cudaGetLastError());
 }
 
+// Degeneracy (batch-peeling) order keys (batch << 32 | id); false if the peel needs more than
+// kMaxPeelBatches batches (then the caller uses the degree order).
+static bool peel_order(nuri_graph* g, uint64_t* keys, cudaStream_t s) {
+  constexpr int kMaxPeelBatches = 20000;
+  const int32_t n = g->d.n;
+  DBuf<int32_t> rem, batch, fa, fb, cnt;
+  rem.alloc(n, s);
+  batch.alloc(n, s);
+  fa.alloc(n, s);
+  fb.alloc(n, s);
+  cnt.alloc(2, s);
+  k_peel_init<<<blocks_for(n), kThreads, 0, s>>>(g->deg.p, n, rem.p, batch.p);
+  int64_t remaining = n;
+  int32_t k = 0, b = 0, nfront = 0;
+  int32_t* front = fa.p;
+  int32_t* next = fb.p;
+  int32_t maxk = 0;
+  while (remaining > 0) {
+    if (b > kMaxPeelBatches) return false;
+    if (nfront == 0) {
+      int32_t init = INT32_MAX;
+      NURI_CUDA(cudaMemcpyAsync(cnt.p, &init, 4, cudaMemcpyHostToDevice, s));
+      k_peel_min<<<blocks_for(n), kThreads, 0, s>>>(rem.p, batch.p, n, cnt.p);
+      int32_t mn = 0;
+      NURI_CUDA(cudaMemcpyAsync(&mn, cnt.p, 4, cudaMemcpyDeviceToHost, s));
+      NURI_CUDA(cudaStreamSynchronize(s));
+      k = std::max(k, mn);
+      NURI_CUDA(cudaMemsetAsync(cnt.p, 0, 4, s));
+      k_peel_select<<<blocks_for(n), kThreads, 0, s>>>(rem.p, batch.p, n, k, b, front, cnt.p);
+      NURI_CUDA(cudaMemcpyAsync(&nfront, cnt.p, 4, cudaMemcpyDeviceToHost, s));
+      NURI_CUDA(cudaStreamSynchronize(s));
+      if (nfront == 0) return false;  // cannot happen while vertices remain
+    }
+    maxk = std::max(maxk, k);
+    NURI_CUDA(cudaMemsetAsync(cnt.p + 1, 0, 4, s));
+    k_peel_remove<<<std::min<int64_t>((nfront + 7) / 8, sm_count() * 16), 256, 0, s>>>(
+        g->off.p, g->adj.p, front, nfront, k, b, rem.p, batch.p, next, cnt.p + 1);
+    remaining -= nfront;
+    int32_t nn = 0;
+    NURI_CUDA(cudaMemcpyAsync(&nn, cnt.p + 1, 4, cudaMemcpyDeviceToHost, s));
+    NURI_CUDA(cudaStreamSynchronize(s));
+    std::swap(front, next);
+    nfront = nn;
+    ++b;
+  }
+  g->degeneracy = maxk;
+  k_peel_keys<<<blocks_for(n), kThreads, 0, s>>>(batch.p, n, keys);
+  return true;
+}
+
 // ---------------------------------------------------------------------------------------------
 void build_graph(nuri_graph* g, int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
                  const uint8_t* labels, const int32_t* weights, int32_t index_hops,
@@ -485,7 +611,8 @@ void build_graph(nuri_graph* g, int32_t n, int64_t m, const int32_t* src, const 
     DBuf<uint64_t> rk, rk2;
     rk.alloc(n, s);
     rk2.alloc(n, s);
-    k_rank_keys<<<blocks_for(n), kThreads, 0, s>>>(g->deg.p, n, rk.p);
+    if (!peel_order(g, rk.p, s))  // very long peels fall back to the (degree, id) order
+      k_rank_keys<<<blocks_for(n), kThreads, 0, s>>>(g->deg.p, n, rk.p);
     size_t t = 0;
     cub::DeviceRadixSort::SortKeys(nullptr, t, rk.p, rk2.p, n, 0, 64, s);
     DBuf<uint8_t> tmp;
@@ -578,6 +705,42 @@ void build_graph(nuri_graph* g, int32_t n, int64_t m, const int32_t* src, const 
       NURI_CUDA(cudaMemsetAsync(g->gmax_w.p, 0xff, sizeof(int32_t) * d.L, s));
       k_gmax<<<blocks_for(n), kThreads, 0, s>>>(g->labels.p, g->weights.p, n, g->gmax_w.p);
       d.gmax_w = g->gmax_w.p;
+    }
+    // vertices grouped by label
+    {
+      DBuf<uint64_t> lk, lk2;
+      lk.alloc(n, s);
+      lk2.alloc(n, s);
+      k_label_keys<<<blocks_for(n), kThreads, 0, s>>>(g->labels.p, n, lk.p);
+      size_t t = 0;
+      cub::DeviceRadixSort::SortKeys(nullptr, t, lk.p, lk2.p, n, 0, 40, s);
+      DBuf<uint8_t> tmp;
+      tmp.alloc(t, s);
+      NURI_CUDA(cub::DeviceRadixSort::SortKeys(tmp.p, t, lk.p, lk2.p, n, 0, 40, s));
+      g->lab_vert.alloc(n, s);
+      DBuf<int32_t> cnt;
+      cnt.alloc(d.L, s);
+      NURI_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * d.L, s));
+      k_label_split<<<blocks_for(n), kThreads, 0, s>>>(lk2.p, n, g->lab_vert.p, cnt.p);
+      std::vector<int32_t> hc(d.L);
+      NURI_CUDA(cudaMemcpyAsync(hc.data(), cnt.p, sizeof(int32_t) * d.L, cudaMemcpyDeviceToHost, s));
+      NURI_CUDA(cudaStreamSynchronize(s));
+      g->h_lab_off.assign(d.L + 1, 0);
+      for (int l = 0; l < d.L; ++l) g->h_lab_off[l + 1] = g->h_lab_off[l] + hc[l];
+      g->lab_off.alloc(d.L + 1, s);
+      NURI_CUDA(cudaMemcpyAsync(g->lab_off.p, g->h_lab_off.data(), sizeof(int64_t) * (d.L + 1),
+                                cudaMemcpyHostToDevice, s));
+      d.lab_off = g->lab_off.p;
+      d.lab_vert = g->lab_vert.p;
+      g->h_gmax_d.resize(d.L);
+      NURI_CUDA(cudaMemcpyAsync(g->h_gmax_d.data(), g->gmax_d.p, sizeof(int32_t) * d.L,
+                                cudaMemcpyDeviceToHost, s));
+      if (weights) {
+        g->h_gmax_w.resize(d.L);
+        NURI_CUDA(cudaMemcpyAsync(g->h_gmax_w.data(), g->gmax_w.p, sizeof(int32_t) * d.L,
+                                  cudaMemcpyDeviceToHost, s));
+      }
+      NURI_CUDA(cudaStreamSynchronize(s));
     }
     if (index_hops > 0) {
       d.H = index_hops;

@@ -79,7 +79,7 @@ struct DBuf {
 // ------------------------------------------------------------------------------------------
 // Layouts (all int32 vertex ids, int64 row offsets):
 //   adj      : undirected CSR, each row sorted by id                  off[n+1], adj[2|E|]
-//   orientation for cliques: rank(v) = position of v in (degree, id) ascending order;
+//   orientation for cliques: rank(v) = position of v in the degeneracy (batch-peeling) order;
 //     oout   : out-rows in rank space, row r = ranks of neighbours with larger rank, sorted
 //     vert_of: rank -> original id
 //   label segments for isomorphism / patterns: the row of v is grouped by neighbour label;
@@ -107,6 +107,8 @@ struct DevGraph {
   const int32_t* idx_d = nullptr;   // hop index over degrees
   const int32_t* gmax_w = nullptr;  // [L] global per-label max weight
   const int32_t* gmax_d = nullptr;  // [L] global per-label max degree
+  const int64_t* lab_off = nullptr; // [L+1] vertices grouped by label
+  const int32_t* lab_vert = nullptr;// [n]   (ascending id inside a label)
   int32_t H = 0;
 };
 
@@ -115,17 +117,20 @@ struct DevGraph {
 struct nuri_graph {
   nuri::DevGraph d;
   int64_t num_edges = 0, dropped = 0;
+  int32_t degeneracy = -1;  // from the peeling order (-1: degree order used)
   cudaStream_t stream = nullptr;
-  nuri::DBuf<int64_t> off, ooff, lsoff;
+  nuri::DBuf<int64_t> off, ooff, lsoff, lab_off;
   nuri::DBuf<int32_t> adj, deg, oout, vert_of, rank_of, weights, idx_w, idx_d, gmax_w, gmax_d;
   nuri::DBuf<uint8_t> labels;
+  nuri::DBuf<int32_t> lab_vert;
+  std::vector<int32_t> h_gmax_w, h_gmax_d;  // host copies of the per-label maxima
+  std::vector<int64_t> h_lab_off;           // host copy of lab_off
   nuri::DBuf<int2> lseg_w, lseg_d;
-  std::vector<int32_t> h_deg_sorted_bounds;  // unused placeholder for host-side caches
   int64_t device_bytes() const {
     return off.bytes() + ooff.bytes() + lsoff.bytes() + adj.bytes() + deg.bytes() +
            oout.bytes() + vert_of.bytes() + rank_of.bytes() + weights.bytes() + idx_w.bytes() +
            idx_d.bytes() + gmax_w.bytes() + gmax_d.bytes() + labels.bytes() + lseg_w.bytes() +
-           lseg_d.bytes();
+           lseg_d.bytes() + lab_off.bytes() + lab_vert.bytes();
   }
 };
 
@@ -172,6 +177,18 @@ struct DevTimer {
     cudaEventDestroy(b);
   }
 };
+
+// process-wide query time budget in nanoseconds (0 = none), set by nuri_set_time_budget
+uint64_t time_budget_ns();
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// writes *deadline = now + budget (or ~0 when budget == 0); launched first by every query
+__global__ void k_set_deadline(uint64_t* deadline, uint64_t budget_ns);
 
 inline int sm_count() {
   static int c = 0;

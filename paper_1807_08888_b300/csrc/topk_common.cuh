@@ -11,19 +11,22 @@ __device__ __forceinline__ int32_t ld_volatile(const int32_t* p) {
   return *(const volatile int32_t*)p;
 }
 
-// Threshold from a score histogram: tau = max t with sum_{s >= t} hist[s] >= k, or INT32_MIN
+// Threshold from a histogram: tau = max t with sum_{s >= t} hist[s] >= k, or INT32_MIN
 // when fewer than k results exist.  Bins may be coarse (score >> shift): the value returned
 // is then the lower edge of the bin, still a valid lower bound of the exact k-th score.
 // Any snapshot of the counters undercounts the final histogram, so every value computed
 // here is <= the final k-th score; publishing it with atomicMax keeps tau monotone.
-__device__ __forceinline__ void publish_threshold(const int32_t* hist, int32_t nbins,
+// The scan starts at `top` (the highest non-empty bin) and stops at the current tau.
+__device__ __forceinline__ void publish_threshold(const int32_t* hist, int32_t top,
                                                   int32_t shift, int64_t k, int32_t* tau) {
+  int32_t cur = ld_volatile(tau);
+  int32_t floor_bin = cur > 0 ? (cur >> shift) : 0;
   int64_t acc = 0;
-  for (int32_t b = nbins - 1; b >= 0; --b) {
+  for (int32_t b = top; b >= floor_bin; --b) {
     acc += ld_volatile(hist + b);
     if (acc >= k) {
       int32_t t = b << shift;
-      if (t > ld_volatile(tau)) atomicMax(tau, t);
+      if (t > cur) atomicMax(tau, t);
       return;
     }
   }

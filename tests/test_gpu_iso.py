@@ -1,0 +1,177 @@
+"""Parity of the CUDA isomorphism path (and hop index) with the oracle; calls go through the
+C ABI.  Integer scores and vertex/edge sets: results must match bit-exactly."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import brute
+
+nuri = pytest.importorskip("paper_1807_08888_b300")
+pytestmark = pytest.mark.gpu
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def load(g, hops=4):
+    return nuri.load_graph(g.n, g.src, g.dst, labels=g.labels, weights=g.weights,
+                           index_hops=hops)
+
+
+def orows(g, q, k, deg=False):
+    return [(r[0], tuple(r[1]), tuple(r[2])) for r in oracle.topk_iso(g, q, k, deg)]
+
+
+def grows(res):
+    return [(r[0], r[1], r[2]) for r in res]
+
+
+def test_fig1b_four_matches():
+    d = json.load(open(os.path.join(GOLD, "fig1b_patterns.json")))
+    e = np.asarray(d["edges"], np.int32)
+    deg = np.bincount(e.ravel(), minlength=d["n"]).astype(np.int32)
+    g = synth.Graph(d["n"], e[:, 0].copy(), e[:, 1].copy(),
+                    labels=np.asarray(d["labels"], np.uint8), weights=deg)
+    G = load(g)
+    q = synth.Query(3, d["iso_query"]["labels"], [tuple(x) for x in d["iso_query"]["edges"]])
+    for degm in (False, True):
+        got = nuri.topk_iso(G, q, 100, degree_rank=degm)
+        assert sorted(list(r[1]) for r in got) == sorted(d["iso_matches_vertex_sets"])
+        assert grows(got) == orows(g, q, 100, degm)
+
+
+def _labelled(n, p, seed, nlab=3, wmax=20):
+    rng = np.random.default_rng(seed)
+    g = synth.er_small(n, p, seed=seed)
+    g.labels = rng.integers(0, nlab, size=n).astype(np.uint8)
+    g.weights = rng.integers(0, wmax + 1, size=n).astype(np.int32)
+    return g
+
+
+def _shapes(rng, nlab, sizes=(1, 2, 3, 4, 5)):
+    out = []
+    for kind in ("path", "cycle", "star", "tree"):
+        for s in sizes:
+            if kind == "cycle" and s < 3:
+                continue
+            out.append(synth.random_query(rng, kind, s, nlab))
+    return out
+
+
+def test_tiny_vs_oracle_and_brute():
+    rng = np.random.default_rng(3)
+    for i in range(40):
+        g = _labelled(int(rng.integers(2, 12)), [0.3, 0.5, 0.8][i % 3], 700 + i)
+        G = load(g, hops=int(rng.integers(0, 4)))
+        for q in _shapes(rng, 3):
+            for k in (1, 5, 100):
+                for degm in (False, True):
+                    want = orows(g, q, k, degm)
+                    got = grows(nuri.topk_iso(G, q, k, degree_rank=degm))
+                    assert got == want, (i, q, k, degm)
+                    if i % 8 == 0 and k == 100:
+                        assert got == [tuple(r) for r in brute.topk_iso(g, q, k, degm)]
+
+
+def test_hop_index_vs_oracle():
+    for i, g in enumerate([_labelled(300, 0.02, 11, nlab=5, wmax=1000),
+                           synth.rmat(11, 8, seed=12)]):
+        if g.labels is None:
+            rng = np.random.default_rng(5)
+            g.labels = rng.integers(0, 8, size=g.n).astype(np.uint8)
+            g.weights = rng.integers(0, 1001, size=g.n).astype(np.int32)
+        G = load(g, hops=4)
+        L = int(g.labels.max()) + 1
+        got = nuri.hop_index(G, 4)
+        want = oracle.hop_index(g, L, 4, method=1)
+        assert np.array_equal(got, want)
+        # degree-scored index
+        gd = synth.Graph(g.n, g.src, g.dst, labels=g.labels,
+                         weights=np.zeros(g.n, np.int32))
+        e = {(min(a, b), max(a, b)) for a, b in zip(g.src.tolist(), g.dst.tolist()) if a != b}
+        deg = np.zeros(g.n, np.int32)
+        for a, b in e:
+            deg[a] += 1
+            deg[b] += 1
+        gd.weights = deg
+        assert np.array_equal(nuri.hop_index(G, 4, degree_rank=True),
+                              oracle.hop_index(gd, L, 4, method=1))
+
+
+def test_hop_index_heavy_rows():
+    # a hub of degree 3000 exercises the one-CTA-per-vertex kernel
+    n = 3100
+    src = np.zeros(3000, np.int32)
+    dst = np.arange(1, 3001, dtype=np.int32)
+    extra = np.arange(3001, 3100, dtype=np.int32)
+    src = np.concatenate([src, extra - 1])
+    dst = np.concatenate([dst, extra])
+    rng = np.random.default_rng(8)
+    g = synth.Graph(n, src, dst, labels=rng.integers(0, 8, size=n).astype(np.uint8),
+                    weights=rng.integers(0, 1001, size=n).astype(np.int32))
+    G = load(g, hops=3)
+    assert np.array_equal(nuri.hop_index(G, 3), oracle.hop_index(g, 8, 3, method=1))
+
+
+def _rmat_labelled(scale, ef, seed, nlab=8):
+    g = synth.rmat(scale, ef, seed=seed)
+    g.labels = synth.labels_uniform(g.n, nlab, seed=seed + 100)
+    g.weights = synth.weights_uniform(g.n, 0, 1000, seed=seed + 200)
+    return g
+
+
+@pytest.mark.parametrize("scale", [10, 12])
+def test_rmat_queries_vs_oracle(scale):
+    g = _rmat_labelled(scale, 16, seed=scale)
+    G = load(g)
+    qs = synth.query_batch(12, seed=scale, size_lo=3, size_hi=6, num_labels=8)
+    for q in qs:
+        for k in (1, 10, 100):
+            assert grows(nuri.topk_iso(G, q, k)) == orows(g, q, k), (q, k)
+
+
+def test_batch_equals_alone():
+    g = _rmat_labelled(11, 16, seed=21)
+    G = load(g)
+    qs = synth.query_batch(16, seed=4, size_lo=3, size_hi=6, num_labels=8)
+    ks = [1, 10, 100, 50] * 4
+    batch = nuri.topk_iso_batch(G, qs, ks)
+    for q, k, b in zip(qs, ks, batch):
+        assert grows(b) == grows(nuri.topk_iso(G, q, k))
+        assert grows(b) == orows(g, q, k)
+
+
+def test_special_cases():
+    g = _rmat_labelled(10, 8, seed=31, nlab=4)
+    G = load(g)
+    # 1-vertex query = sort of the label class by weight
+    q = synth.Query(1, [2], [])
+    v = np.flatnonzero(g.labels == 2)
+    order = sorted(v.tolist(), key=lambda x: (-int(g.weights[x]), x))[:30]
+    assert grows(nuri.topk_iso(G, q, 30)) == [(int(g.weights[x]), (x,), ()) for x in order]
+    # label absent from the graph: no match, no error
+    assert list(nuri.topk_iso(G, synth.Query(2, [1, 9], [(0, 1)]), 5)) == []
+    # a disconnected query is rejected
+    with pytest.raises(nuri.NuriError):
+        nuri.topk_iso(G, synth.Query(3, [0, 1, 2], [(0, 1)]), 5)
+    with pytest.raises(nuri.NuriError):
+        nuri.topk_iso(G, synth.Query(9, [0] * 9, [(i, i + 1) for i in range(8)]), 5)
+
+
+def test_keep_ties_and_restart(monkeypatch):
+    g = _labelled(60, 0.2, 41, nlab=2, wmax=3)   # many equal scores
+    G = load(g)
+    q = synth.path_query([0, 1, 0])
+    allr = brute.topk_iso(g, q, 10 ** 9)
+    for k in (1, 7, 40):
+        tau = allr[k - 1][0]
+        want = [tuple(r) for r in allr if r[0] >= tau]
+        assert grows(nuri.topk_iso(G, q, k, keep_ties=True)) == want
+    monkeypatch.setenv("NURI_RESULT_CAP", "8")
+    got = nuri.topk_iso(G, q, 40)
+    monkeypatch.delenv("NURI_RESULT_CAP")
+    assert got.stats["restarts"] >= 1
+    assert grows(got) == [tuple(r) for r in allr[:40]]
