@@ -264,17 +264,63 @@ def main():
         dist.destroy_process_group()
 
 
+def _ms(r):
+    return r.stats["device_ms"]
+
+
 def extra_workloads(nuri, torch, sptr):
+    """The other configurations: ER planted clique, the 64-query isomorphism batch (batched
+    launch vs one query at a time), and pattern mining M = 1..5."""
     import synth
     out = {}
     g = synth.workload("er2000")
     G = nuri.load_graph(g.n, g.src, g.dst, stream=sptr)
-    for _ in range(2):
+    for _ in range(3):
         nuri.topk_cliques(G, 10, stream=sptr)
     r = nuri.topk_cliques(G, 10, stream=sptr)
-    out["er2000_top10_cliques"] = {"time_to_topk_ms": r.stats["device_ms"],
-                                   "expansions": r.stats["expansions"],
-                                   "expansions_per_s": r.stats["expansions"] / (r.stats["device_ms"] / 1e3)}
+    out["er2000_top10_cliques"] = {"time_to_topk_ms": _ms(r), "expansions": r.stats["expansions"],
+                                   "expansions_per_s": r.stats["expansions"] / (_ms(r) / 1e3)}
+    G.free()
+
+    g = synth.workload("rmat20")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    G = nuri.load_graph(g.n, g.src, g.dst, labels=g.labels, weights=g.weights, index_hops=4,
+                        stream=sptr)
+    load_s = time.perf_counter() - t0
+    qs = synth.query_batch(64, seed=1)
+    ks = [1000] * 64
+    nuri.topk_iso_batch(G, qs, ks, stream=sptr)  # warm-up
+    bt = []
+    for _ in range(3):
+        rb = nuri.topk_iso_batch(G, qs, ks, stream=sptr)
+        bt.append(_ms(rb[0]))
+    exp_b = rb[0].stats["expansions"]
+    plain_ms, exp_p = 0.0, 0
+    for q in qs:
+        rp = nuri.topk_iso(G, q, 1000, stream=sptr)
+        plain_ms += _ms(rp)
+        exp_p += rp.stats["expansions"]
+    bms = float(np.median(bt))
+    out["rmat20_iso64_top1000"] = {
+        "batched_time_to_topk_ms": bms, "plain_time_to_topk_ms": plain_ms,
+        "batched_expansions_per_s": exp_b / (bms / 1e3),
+        "plain_expansions_per_s": exp_p / (plain_ms / 1e3),
+        "batched_speedup": plain_ms / bms, "expansions_batched": exp_b,
+        "expansions_plain": exp_p, "graph_load_and_index_s": load_s,
+        "edges": G.info()["num_edges"]}
+    G.free()
+
+    g = synth.workload("rmat18z")
+    G = nuri.load_graph(g.n, g.src, g.dst, labels=g.labels, stream=sptr)
+    pm = {}
+    for M in (1, 2, 3, 4, 5):
+        nuri.topk_patterns(G, M, 10, stream=sptr)
+        r = nuri.topk_patterns(G, M, 10, stream=sptr)
+        pm[f"M{M}"] = {"time_to_topk_ms": _ms(r), "top_support": r[0][0] if r else None,
+                       "kth_support": r[-1][0] if r else None, "candidates": r.stats["expansions"]}
+    out["rmat18z_top10_patterns"] = pm
+    G.free()
     return out
 
 

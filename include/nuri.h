@@ -46,6 +46,7 @@ typedef int32_t nuri_status;
 #define NURI_ERR_TIMEOUT 4   /* the query ran past its time budget (nuri_set_time_budget)  */
 #define NURI_ERR_CANCELLED 5 /* the request was cancelled                                  */
 #define NURI_ERR_CUDA 6      /* a CUDA runtime call failed                                 */
+#define NURI_PENDING 7       /* nuri_server_poll: the request has not finished yet         */
 
 /* ranking functions */
 #define NURI_RANK_SIZE 0        /* cliques: |V_s|                                           */
@@ -205,6 +206,63 @@ nuri_status nuri_hop_index(nuri_graph* g, int32_t hops, int32_t degree_rank, int
 nuri_status nuri_set_time_budget(double ms);
 
 void nuri_free_result(nuri_result* r);
+
+/* ---- serving: continuous batching over one resident graph ------------------------------ */
+
+#define NURI_REQ_CLIQUES 0
+#define NURI_REQ_ISO 1
+
+/* One request: kind NURI_REQ_CLIQUES (rank NURI_RANK_SIZE, flags as nuri_topk_cliques) or
+ * NURI_REQ_ISO (query, rank WEIGHT_SUM or DEGREE_SUM, flags as nuri_topk_iso).  The query
+ * arrays are copied at submission. */
+typedef struct nuri_request {
+  int32_t kind;
+  int32_t k;
+  int32_t rank;
+  uint32_t flags;
+  nuri_query query;
+} nuri_request;
+
+/* slots: concurrent requests (one CUDA stream and one host worker each, default 4);
+ * max_batch: isomorphism requests merged into one launch (default 64);
+ * mem_budget_bytes: device memory admitted requests may hold together (default 8 GiB). */
+typedef struct nuri_server_cfg {
+  int32_t slots;
+  int32_t max_batch;
+  int64_t mem_budget_bytes;
+} nuri_server_cfg;
+
+/* Host-clock times of a finished request: waiting for admission, running, and both. */
+typedef struct nuri_request_times {
+  double queue_ms;
+  double service_ms;
+  double total_ms;
+} nuri_request_times;
+
+typedef struct nuri_server nuri_server;
+
+/*
+ * nuri_server_create -- start a request server on a loaded graph (the graph must outlive it).
+ * Requests are admitted oldest first as soon as a slot is free and their device-memory
+ * estimate fits the budget; isomorphism requests waiting together run as one batched launch
+ * (the frontier-level batching of nuri_topk_iso_batch).  Results are identical to the same
+ * query run alone.
+ */
+nuri_status nuri_server_create(nuri_graph* g, const nuri_server_cfg* cfg, nuri_server** out);
+/* Queue a request (thread-safe); *ticket identifies it. */
+nuri_status nuri_server_submit(nuri_server* s, const nuri_request* r, uint64_t* ticket);
+/* Non-blocking: NURI_PENDING while running; otherwise the request's status, its result in
+ * *out (caller frees with nuri_free_result) and its times (times may be NULL).  A ticket is
+ * reported once. */
+nuri_status nuri_server_poll(nuri_server* s, uint64_t ticket, nuri_result** out,
+                             nuri_request_times* times);
+/* Blocking variant of nuri_server_poll. */
+nuri_status nuri_server_wait(nuri_server* s, uint64_t ticket, nuri_result** out,
+                             nuri_request_times* times);
+/* Number of batched isomorphism launches and of requests they carried. */
+nuri_status nuri_server_stats(nuri_server* s, int64_t* batches, int64_t* batched);
+/* Finish every queued request, stop the workers, free unclaimed results. */
+void nuri_server_destroy(nuri_server* s);
 
 /* Message of the last failure on the calling thread ("" if none). */
 const char* nuri_last_error(void);

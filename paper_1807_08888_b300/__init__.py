@@ -20,14 +20,15 @@ import numpy as np
 
 __all__ = [
     "NuriError", "lib", "load_graph", "Graph", "topk_cliques", "topk_iso", "topk_iso_batch",
-    "topk_patterns", "hop_index", "set_time_budget", "Result", "LIB_PATH", "EXPORTS",
+    "topk_patterns", "hop_index", "set_time_budget", "Server", "Result", "LIB_PATH", "EXPORTS",
     "RANK_SIZE", "RANK_WEIGHT_SUM", "RANK_DEGREE_SUM", "RANK_MNI",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libnuri.so")
 
-OK, ERR_INVALID, ERR_OOM, ERR_LIMIT, ERR_TIMEOUT, ERR_CANCELLED, ERR_CUDA = range(7)
+OK, ERR_INVALID, ERR_OOM, ERR_LIMIT, ERR_TIMEOUT, ERR_CANCELLED, ERR_CUDA, PENDING = range(8)
+REQ_CLIQUES, REQ_ISO = 0, 1
 RANK_SIZE, RANK_WEIGHT_SUM, RANK_DEGREE_SUM, RANK_MNI = range(4)
 LOAD_DEVICE_INPUT, LOAD_NO_ISO = 0x1, 0x2
 CLIQUE_ALL, CLIQUE_MAXIMAL = 0x0, 0x1
@@ -38,6 +39,8 @@ EXPORTS = (
     "nuri_load_graph", "nuri_free_graph", "nuri_graph_get_info", "nuri_topk_cliques",
     "nuri_topk_iso", "nuri_topk_iso_batch", "nuri_topk_patterns", "nuri_hop_index",
     "nuri_free_result", "nuri_last_error", "nuri_version", "nuri_set_time_budget",
+    "nuri_server_create", "nuri_server_submit", "nuri_server_poll", "nuri_server_wait",
+    "nuri_server_stats", "nuri_server_destroy",
 )
 
 
@@ -75,6 +78,21 @@ class _Query(ctypes.Structure):
         ("nq", ctypes.c_int32), ("ne", ctypes.c_int32),
         ("labels", ctypes.c_void_p), ("src", ctypes.c_void_p), ("dst", ctypes.c_void_p),
     ]
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("k", ctypes.c_int32), ("rank", ctypes.c_int32),
+                ("flags", ctypes.c_uint32), ("query", _Query)]
+
+
+class _ServerCfg(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("mem_budget_bytes", ctypes.c_int64)]
+
+
+class _Times(ctypes.Structure):
+    _fields_ = [("queue_ms", ctypes.c_double), ("service_ms", ctypes.c_double),
+                ("total_ms", ctypes.c_double)]
 
 
 class _Info(ctypes.Structure):
@@ -121,6 +139,21 @@ def lib():
             L.nuri_hop_index.restype = i32
             L.nuri_set_time_budget.argtypes = [ctypes.c_double]
             L.nuri_set_time_budget.restype = i32
+            L.nuri_server_create.argtypes = [P, ctypes.POINTER(_ServerCfg),
+                                             ctypes.POINTER(ctypes.c_void_p)]
+            L.nuri_server_create.restype = i32
+            L.nuri_server_submit.argtypes = [P, ctypes.POINTER(_Request),
+                                             ctypes.POINTER(ctypes.c_uint64)]
+            L.nuri_server_submit.restype = i32
+            for nm in ("nuri_server_poll", "nuri_server_wait"):
+                f = getattr(L, nm)
+                f.argtypes = [P, ctypes.c_uint64, RPP, ctypes.POINTER(_Times)]
+                f.restype = i32
+            L.nuri_server_stats.argtypes = [P, ctypes.POINTER(ctypes.c_int64),
+                                            ctypes.POINTER(ctypes.c_int64)]
+            L.nuri_server_stats.restype = i32
+            L.nuri_server_destroy.argtypes = [P]
+            L.nuri_server_destroy.restype = None
             L.nuri_free_result.argtypes = [ctypes.POINTER(_Result)]
             L.nuri_free_result.restype = None
             L.nuri_last_error.restype = ctypes.c_char_p
@@ -293,6 +326,68 @@ def hop_index(g: Graph, hops: int, degree_rank=False, stream=None) -> np.ndarray
     _check(lib().nuri_hop_index(g.handle, int(hops), int(bool(degree_rank)),
                                 out.ctypes.data_as(ctypes.c_void_p), 0, _stream(stream)))
     return out
+
+
+class Server:
+    """Continuous-batching request server over a resident graph (nuri_server_*)."""
+
+    def __init__(self, g: Graph, slots=4, max_batch=64, mem_budget_bytes=8 << 30):
+        self._g = g  # keep the graph alive
+        cfg = _ServerCfg(int(slots), int(max_batch), int(mem_budget_bytes))
+        h = ctypes.c_void_p()
+        _check(lib().nuri_server_create(g.handle, ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+
+    def submit_cliques(self, k, maximal=False) -> int:
+        r = _Request(REQ_CLIQUES, int(k), RANK_SIZE, CLIQUE_MAXIMAL if maximal else 0,
+                     _Query(0, 0, None, None, None))
+        t = ctypes.c_uint64()
+        _check(lib().nuri_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
+        return t.value
+
+    def submit_iso(self, q, k, degree_rank=False) -> int:
+        keep = []
+        r = _Request(REQ_ISO, int(k), RANK_DEGREE_SUM if degree_rank else RANK_WEIGHT_SUM, 0,
+                     _query_struct(q, keep))
+        t = ctypes.c_uint64()
+        _check(lib().nuri_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket):
+        """(result, times) when finished, None while pending; raises on a failed request."""
+        rp = ctypes.POINTER(_Result)()
+        tm = _Times()
+        rc = lib().nuri_server_poll(self._h, ctypes.c_uint64(ticket), ctypes.byref(rp),
+                                    ctypes.byref(tm))
+        if rc == PENDING:
+            return None
+        _check(rc)
+        return _unpack(rp), {"queue_ms": tm.queue_ms, "service_ms": tm.service_ms,
+                             "total_ms": tm.total_ms}
+
+    def wait(self, ticket):
+        rp = ctypes.POINTER(_Result)()
+        tm = _Times()
+        _check(lib().nuri_server_wait(self._h, ctypes.c_uint64(ticket), ctypes.byref(rp),
+                                      ctypes.byref(tm)))
+        return _unpack(rp), {"queue_ms": tm.queue_ms, "service_ms": tm.service_ms,
+                             "total_ms": tm.total_ms}
+
+    def stats(self):
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().nuri_server_stats(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return {"iso_batches": a.value, "iso_batched_requests": b.value}
+
+    def close(self):
+        if self._h:
+            lib().nuri_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def set_time_budget(ms: float) -> None:

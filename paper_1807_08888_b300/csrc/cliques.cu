@@ -32,6 +32,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <vector>
@@ -46,7 +47,6 @@ constexpr int MAXD = 128;      // largest clique the records can hold
 constexpr int BM = 64;         // bitmap tail handles |P| <= BM
 constexpr int NB = 256;        // frontier buckets (bucket NB-1 holds every bound >= NB-1;
                                // cliques never exceed MAXD < NB-1, so the order is exact)
-constexpr int WARPS = 4;       // warps per CTA of the expansion kernel
 constexpr int PSMEM = 512;     // P entries staged in shared memory per warp
 
 struct Rec {
@@ -61,6 +61,7 @@ struct QState {
   int64_t res_count;     // results appended (may exceed the capacity: then a re-run)
   int64_t stage_count;   // children slots reserved in the staging array
   int64_t defer_count;   // parents sent back because the staging array was full
+  int64_t wide_count;    // records handed to the wide bitmap tail
   int64_t work_next;     // dynamic work counter
   unsigned long long expansions, pruned, dequeued, adj_bytes;
   int32_t hmax;          // largest clique size recorded so far
@@ -129,12 +130,14 @@ struct Ctx {
   Rec* stage;
   int64_t stage_cap;
   Rec* deferred;
+  Rec* wide;            // records for the wide bitmap tail (64 < |P| <= 64 KWIDE)
   int32_t* pscratch;    // per-warp global P buffer (max_out entries each)
   int64_t pscratch_stride;
   int32_t k;
   int32_t maximal;
   int32_t no_prune;
   const uint64_t* deadline;  // global timer value after which the query stops (err bit 2)
+  int32_t split_above;       // records with more candidates than this are split
 };
 
 __device__ __forceinline__ bool past_deadline(const Ctx& cx) {
@@ -163,14 +166,56 @@ __device__ void add_result(const Ctx& cx, const int32_t* V, int nv, int32_t extr
 // Expansion kernel: one warp per record (dynamic assignment).
 //   seeds != nullptr: record i is the seed vertex seeds[i] (nv = 1)
 //   otherwise       : record i is in[i]
+// W = 64-bit words of the bitmap tail: records with |P| <= 64 W are finished in the warp.
+// The W = 1 instantiation hands records with 64 < |P| <= 64 KWIDE to the wide instantiation
+// (cx.wide list) and splits records with larger |P|; the wide one splits only the latter.
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(WARPS * 32) k_clique_expand(Ctx cx, const Rec* __restrict__ in,
-                                                              const int32_t* __restrict__ seeds,
-                                                              int64_t nin) {
-  __shared__ int32_t sP[WARPS][PSMEM];
-  __shared__ unsigned long long sRow[WARPS][BM];   // neighbours with a larger index in P
-  __shared__ unsigned long long sFull[WARPS][BM];  // all neighbours inside P
-  __shared__ int32_t sV[WARPS][MAXD];
+constexpr int KWIDE = 8;
+
+template <int W>
+struct KCfg {
+  static constexpr int WARPS = 4;
+};
+template <>
+struct KCfg<KWIDE> {
+  static constexpr int WARPS = 2;
+};
+
+template <int W>
+__device__ __forceinline__ int lowest(const unsigned long long* X, int wa) {
+#pragma unroll
+  for (int q = 0; q < W; ++q)
+    if (q < wa && X[q]) return q * 64 + __ffsll((long long)X[q]) - 1;
+  return -1;
+}
+
+template <int W>
+__device__ __forceinline__ int popc(const unsigned long long* X, int wa) {
+  int c = 0;
+#pragma unroll
+  for (int q = 0; q < W; ++q)
+    if (q < wa) c += __popcll(X[q]);
+  return c;
+}
+
+template <int W>
+__device__ __forceinline__ bool any(const unsigned long long* X, int wa) {
+  unsigned long long a = 0;
+#pragma unroll
+  for (int q = 0; q < W; ++q)
+    if (q < wa) a |= X[q];
+  return a != 0;
+}
+
+template <int W>
+__global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
+    k_clique_expand(Ctx cx, const Rec* __restrict__ in, const int32_t* __restrict__ seeds,
+                    int64_t nin) {
+  constexpr int NW = KCfg<W>::WARPS;
+  constexpr int BMW = 64 * W;   // candidates the bitmap tail handles
+  __shared__ int32_t sP[NW][PSMEM];
+  __shared__ int32_t sV[NW][MAXD];
+  extern __shared__ unsigned long long dynrows[];  // NW * BMW * W words: upper rows of P
 
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
@@ -178,6 +223,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_clique_expand(Ctx cx, const Rec*
   const DevGraph& g = cx.g;
   const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int32_t* scratch = cx.pscratch ? cx.pscratch + gwarp * cx.pscratch_stride : nullptr;
+  unsigned long long* rows = dynrows + (size_t)w * BMW * W;  // row i = rows[i*W .. i*W+W)
 
   unsigned long long my_exp = 0, my_pruned = 0, my_deq = 0, my_bytes = 0;
 
@@ -267,10 +313,23 @@ __global__ void __launch_bounds__(WARPS * 32) k_clique_expand(Ctx cx, const Rec*
       if (lane == 0) atomicOr(&cx.st->err, 1);
       continue;
     }
+    // a record for the wide bitmap tail goes to its list untouched (dequeued there)
+    const int lim = BMW < cx.split_above ? BMW : cx.split_above;  // bitmap tail limit here
+    if (W == 1 && p > lim && p <= 64 * KWIDE && p <= cx.split_above) {
+      if (lane == 0) {
+        int64_t ds = (int64_t)atomicAdd((unsigned long long*)&cx.st->wide_count, 1ull);
+        Rec* r = cx.wide + ds;
+        r->nv = nv;
+        r->bound = bound;
+        for (int i = 0; i < nv; ++i) r->V[i] = sV[w][i];
+        --my_deq;
+      }
+      continue;
+    }
     // a record that must be split reserves its children's staging slots first; if the
     // staging array is full it goes back to the frontier untouched (re-dequeued later)
     int64_t base_slot = 0;
-    if (p > BM) {
+    if (p > lim) {
       bool reserved = true;
       if (lane == 0) {
         base_slot = (int64_t)atomicAdd((unsigned long long*)&cx.st->stage_count,
@@ -296,8 +355,9 @@ __global__ void __launch_bounds__(WARPS * 32) k_clique_expand(Ctx cx, const Rec*
     }
     if (p == 0) continue;
 
-    if (p <= BM) {
+    if (p <= lim) {
       // ================= bitmap tail: finish the whole subtree in this warp =================
+      const int wa = (p + 63) >> 6;  // words in use
       int32_t* sp = sP[w];
       if (P != sp) {
         for (int i = lane; i < p; i += 32) sp[i] = P[i];
@@ -308,81 +368,88 @@ __global__ void __launch_bounds__(WARPS * 32) k_clique_expand(Ctx cx, const Rec*
       for (int i = 0; i < p; ++i) {
         int32_t v = sp[i];
         int64_t rb = g.ooff[v], re = g.ooff[v + 1];
-        unsigned long long bits = 0;
+        unsigned long long bits[W];
+#pragma unroll
+        for (int q = 0; q < W; ++q) bits[q] = 0;
         int64_t scanned = 0;
         for (int64_t base = rb; base < re; base += 32) {
           int64_t t = base + lane;
           int32_t x = t < re ? __ldg(g.oout + t) : INT32_MAX;
           if (x <= plast) {
             int j = lower_bound_dev(sp, i + 1, p, x);
-            if (j < p && sp[j] == x) bits |= 1ull << j;
+            if (j < p && sp[j] == x) {
+#pragma unroll
+              for (int q = 0; q < W; ++q)
+                if ((j >> 6) == q) bits[q] |= 1ull << (j & 63);
+            }
           }
           scanned += 32;
           // rows are sorted: stop once the whole chunk is past the last candidate
           if (__all_sync(FULL, x > plast)) break;
         }
-        unsigned lo = __reduce_or_sync(FULL, (unsigned)bits);
-        unsigned hi = __reduce_or_sync(FULL, (unsigned)(bits >> 32));
-        if (lane == 0) {
-          sRow[w][i] = ((unsigned long long)hi << 32) | lo;
-          my_bytes += 4ull * (unsigned long long)(scanned < re - rb ? scanned : re - rb);
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+          if (q >= wa) break;
+          unsigned lo = __reduce_or_sync(FULL, (unsigned)bits[q]);
+          unsigned hi = __reduce_or_sync(FULL, (unsigned)(bits[q] >> 32));
+          if (lane == 0) rows[i * W + q] = ((unsigned long long)hi << 32) | lo;
         }
+        if (lane == 0) my_bytes += 4ull * (unsigned long long)(scanned < re - rb ? scanned : re - rb);
       }
       __syncwarp();
-      // symmetric rows for the colouring bound
-      for (int j = lane; j < p; j += 32) {
-        unsigned long long f = sRow[w][j];
-        for (int i = 0; i < j; ++i) f |= ((sRow[w][i] >> j) & 1ull) << i;
-        sFull[w][j] = f;
-      }
-      __syncwarp();
-      // lane-parallel depth-first search: lane owns the children j = lane, lane + 32.
-      // Per-lane stack (local memory): stk[d] = untried candidates of the node at depth d,
-      // pick[d] = index in P of the vertex added at depth d (depth <= |P| <= 64).
-      bool limit_hit = false;
-      unsigned long long stk[BM];
-      uint8_t pick[BM + 1];
       // Lane tasks: task j < p is the child node {P_j} alone; the other tasks are the
       // subtrees rooted at the grandchildren {P_j, P_b} (b in row[j]), so a dense child's
       // subtree is spread over many lanes.  Every node is visited by exactly one task.
       int ntask = p;
-      for (int j = 0; j < p; ++j) ntask += __popcll(sRow[w][j]);
-      bool out_of_time = false;
+      for (int j = 0; j < p; ++j) ntask += popc<W>(rows + j * W, wa);
+      bool limit_hit = false, out_of_time = false;
       int32_t t_cache = ld_volatile(&cx.st->tau);
       int tj = 0, tb = -1;  // (j, b) of the task with index tnext
       int tnext = 0;
+      // per-lane DFS state: pick[d] = index in P added at depth d; for W == 1 the untried
+      // siblings of depth d are kept in stk[d], for wider masks they are recomputed from rows
+      uint16_t pick[BMW + 1];
+      unsigned long long stk[W == 1 ? BMW : 1];
       for (int task = lane; task < ntask && !out_of_time; task += 32) {
         int depth;
-        unsigned long long X;
+        unsigned long long X[W];
         if (task < p) {
           depth = 0;
-          pick[0] = (uint8_t)task;
-          X = sRow[w][task];
+          pick[0] = (uint16_t)task;
+#pragma unroll
+          for (int q = 0; q < W; ++q) X[q] = rows[task * W + q];
         } else {
           // walk the (j, b) enumeration forward to index `task`
           if (tnext < p) {
             tnext = p;
             tj = 0;
-            while (sRow[w][tj] == 0) ++tj;
-            tb = __ffsll((long long)sRow[w][tj]) - 1;
+            while (!any<W>(rows + tj * W, wa)) ++tj;
+            tb = lowest<W>(rows + tj * W, wa);
           }
           while (tnext < task) {
-            unsigned long long rest = tb >= 63 ? 0ull : (sRow[w][tj] & ~((2ull << tb) - 1));
-            if (rest) {
-              tb = __ffsll((long long)rest) - 1;
+            // next set bit of row tj after tb, else the first bit of the next non-empty row
+            int nb = -1;
+            for (int q = (tb + 1) >> 6; q < wa && nb < 0; ++q) {
+              unsigned long long m = rows[tj * W + q];
+              if (q == ((tb + 1) >> 6)) m = ((tb + 1) & 63) ? (m & ~((1ull << ((tb + 1) & 63)) - 1)) : m;
+              if (m) nb = q * 64 + __ffsll((long long)m) - 1;
+            }
+            if (nb >= 0) {
+              tb = nb;
             } else {
               do {
                 ++tj;
-              } while (sRow[w][tj] == 0);
-              tb = __ffsll((long long)sRow[w][tj]) - 1;
+              } while (!any<W>(rows + tj * W, wa));
+              tb = lowest<W>(rows + tj * W, wa);
             }
             ++tnext;
           }
           depth = 1;
-          pick[0] = (uint8_t)tj;
-          pick[1] = (uint8_t)tb;
-          X = sRow[w][tj] & sRow[w][tb];
-          stk[0] = 0;  // the siblings of this grandchild are other tasks
+          pick[0] = (uint16_t)tj;
+          pick[1] = (uint16_t)tb;
+#pragma unroll
+          for (int q = 0; q < W; ++q) X[q] = rows[tj * W + q] & rows[tb * W + q];
+          if (W == 1) stk[0] = 0;  // the siblings of this grandchild are other tasks
         }
         const bool single = task < p;  // a child task visits its own node only
         while (true) {
@@ -398,21 +465,30 @@ __global__ void __launch_bounds__(WARPS * 32) k_clique_expand(Ctx cx, const Rec*
             }
           }
           int32_t t_now = t_cache;
-          int bnd = size + __popcll(X);
+          int bnd = size + popc<W>(X, wa);
           // a greedy colouring of the candidates bounds the clique they can add (a clique
-          // takes at most one vertex per colour class); tighter than |P| on dense candidates
-          if (!cx.no_prune && bnd >= t_now && X != 0 && bnd - 1 > size) {
+          // takes at most one vertex per colour class); tighter than |P| on dense candidates.
+          // Classes are built in index order, so the upper rows suffice: a vertex leaves the
+          // class being built as soon as a lower-index member is adjacent to it.
+          if (!cx.no_prune && bnd >= t_now && bnd - 1 > size) {
             int colours = 0;
-            unsigned long long left = X;
-            while (left) {
+            unsigned long long left[W];
+#pragma unroll
+            for (int q = 0; q < W; ++q) left[q] = X[q];
+            while (any<W>(left, wa) && size + colours < t_now) {
               ++colours;
-              unsigned long long cls = left;
-              while (cls) {
-                int v = __ffsll((long long)cls) - 1;
-                cls &= ~sFull[w][v] & ~(1ull << v);
-                left &= ~(1ull << v);
+              unsigned long long cls[W];
+#pragma unroll
+              for (int q = 0; q < W; ++q) cls[q] = left[q];
+              int v;
+              while ((v = lowest<W>(cls, wa)) >= 0) {
+#pragma unroll
+                for (int q = 0; q < W; ++q) cls[q] &= ~rows[v * W + q];
+                cls[v >> 6] &= ~(1ull << (v & 63));
+                left[v >> 6] &= ~(1ull << (v & 63));
               }
             }
+            if (any<W>(left, wa)) colours += 1;  // stopped early: the bound already reaches tau
             bnd = size + colours;
           }
           bool expand_node = !single;
@@ -421,10 +497,10 @@ __global__ void __launch_bounds__(WARPS * 32) k_clique_expand(Ctx cx, const Rec*
             expand_node = false;
           } else if (size >= t_now) {
             bool rel = true;
-            int32_t pick_ranks[BM];
+            int32_t pick_ranks[MAXD];
             for (int d = 0; d <= depth; ++d) pick_ranks[d] = sp[pick[d]];
             if (cx.maximal) {
-              if (X != 0) rel = false;
+              if (any<W>(X, wa)) rel = false;
               else {
                 int32_t C[MAXD];
                 for (int i = 0; i < nv; ++i) C[i] = sV[w][i];
@@ -437,18 +513,19 @@ __global__ void __launch_bounds__(WARPS * 32) k_clique_expand(Ctx cx, const Rec*
               t_cache = ld_volatile(&cx.st->tau);
             }
           }
-          if (expand_node && X != 0 && size >= MAXD) {
+          if (expand_node && any<W>(X, wa) && size >= MAXD) {
             limit_hit = true;
             expand_node = false;
           }
-          if (expand_node && X != 0) {
-            // descend into the lowest candidate, keep the rest for the siblings
-            int b = __ffsll((long long)X) - 1;
-            unsigned long long rest = X & (X - 1);
-            stk[depth] = rest;
+          if (expand_node && any<W>(X, wa)) {
+            // descend into the lowest candidate; the others are its later siblings
+            int b = lowest<W>(X, wa);
+            if (W == 1) stk[depth] = X[0] & (X[0] - 1);
             ++depth;
-            pick[depth] = (uint8_t)b;
-            X = rest & sRow[w][b];
+            pick[depth] = (uint16_t)b;
+#pragma unroll
+            for (int q = 0; q < W; ++q) X[q] &= rows[b * W + q];
+            X[b >> 6] &= ~(1ull << (b & 63));
             continue;
           }
           if (single) break;
@@ -459,17 +536,33 @@ __global__ void __launch_bounds__(WARPS * 32) k_clique_expand(Ctx cx, const Rec*
               done = true;
               break;
             }
-            unsigned long long rest = stk[depth - 1];
+            // untried siblings of the node at `depth`: candidates of its parent after it
+            unsigned long long rest[W];
+            if (W == 1) {
+              rest[0] = stk[depth - 1];
+            } else {
+#pragma unroll
+              for (int q = 0; q < W; ++q) rest[q] = rows[pick[0] * W + q];
+              for (int d = 1; d < depth; ++d)
+#pragma unroll
+                for (int q = 0; q < W; ++q) rest[q] &= rows[pick[d] * W + q];
+              int c = pick[depth];  // clear every bit <= c
+#pragma unroll
+              for (int q = 0; q < W; ++q) {
+                if (q < (c >> 6)) rest[q] = 0;
+                else if (q == (c >> 6)) rest[q] &= ((c & 63) == 63) ? 0ull : ~((2ull << (c & 63)) - 1);
+              }
+            }
             int parent_size = nv + depth;  // size of the node whose children are iterated
-            if (rest == 0 || (!cx.no_prune && parent_size + __popcll(rest) < t_cache)) {
+            if (!any<W>(rest, wa) || (!cx.no_prune && parent_size + popc<W>(rest, wa) < t_cache)) {
               --depth;
               continue;
             }
-            int b = __ffsll((long long)rest) - 1;
-            unsigned long long rest2 = rest & (rest - 1);
-            stk[depth - 1] = rest2;
-            pick[depth] = (uint8_t)b;
-            X = rest2 & sRow[w][b];
+            int b = lowest<W>(rest, wa);
+            if (W == 1) stk[depth - 1] = rest[0] & (rest[0] - 1);
+            pick[depth] = (uint16_t)b;
+#pragma unroll
+            for (int q = 0; q < W; ++q) X[q] = rest[q] & rows[b * W + q];
             break;
           }
           if (done) break;
@@ -562,10 +655,15 @@ __global__ void __launch_bounds__(WARPS * 32) k_clique_expand(Ctx cx, const Rec*
 // ---------------------------------------------------------------------------------------------
 __device__ __forceinline__ int bucket_of(int32_t bound) { return bound >= NB - 1 ? NB - 1 : bound; }
 
+// Seed key = (class << 24) | bound, bound = 1 + |N+(v)|.  Class 1: the candidate set fits the
+// narrow bitmap tail (|N+(v)| <= 64).  Seeds are consumed class 1 first, each class in
+// descending bound order: the narrow seeds are cheap and usually raise tau to its final
+// value (planted or core cliques), so the wide, dense seeds are searched under a high tau.
 __global__ void k_seed_bounds(DevGraph g, int32_t* keys, int32_t* vals) {
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < g.n;
        r += (int64_t)gridDim.x * blockDim.x) {
-    keys[r] = 1 + (int32_t)(g.ooff[r + 1] - g.ooff[r]);
+    int32_t outdeg = (int32_t)(g.ooff[r + 1] - g.ooff[r]);
+    keys[r] = ((outdeg <= 64 ? 1 : 0) << 24) | (1 + outdeg);
     vals[r] = (int32_t)r;
   }
 }
@@ -573,7 +671,7 @@ __global__ void k_seed_bounds(DevGraph g, int32_t* keys, int32_t* vals) {
 __global__ void k_bucket_hist(const int32_t* keys, int64_t n, int32_t* hist) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    atomicAdd(&hist[bucket_of(keys[i])], 1);
+    atomicAdd(&hist[(keys[i] >> 24) * NB + bucket_of(keys[i] & 0xffffff)], 1);
 }
 
 __global__ void k_stage_hist(const Rec* stage, int64_t cnt, int32_t* hist) {
@@ -664,6 +762,34 @@ inline int grid_for(int64_t n) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(b, 1 << 20));
 }
 
+// Narrow expansion over the batch, then the wide bitmap tail over the records it handed on.
+// The events bracket both launches (the expansion time of the round).
+int64_t launch_expand(Ctx cx, const Rec* in, const int32_t* seeds, int64_t nin, int grid,
+                      DBuf<Rec>& wide, cudaEvent_t ev0, cudaEvent_t ev1, cudaStream_t s) {
+  const size_t dyn1 = sizeof(unsigned long long) * KCfg<1>::WARPS * 64;
+  const size_t dynw = sizeof(unsigned long long) * KCfg<KWIDE>::WARPS * 64 * KWIDE * KWIDE;
+  static const cudaError_t attr = cudaFuncSetAttribute(  // once per process (thread-safe init)
+      k_clique_expand<KWIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dynw);
+  NURI_CUDA(attr);
+  cx.wide = wide.p;
+  NURI_CUDA(cudaEventRecord(ev0, s));
+  k_clique_expand<1><<<grid, KCfg<1>::WARPS * 32, dyn1, s>>>(cx, in, seeds, nin);
+  NURI_CUDA(cudaGetLastError());
+  int64_t nw = 0;
+  NURI_CUDA(cudaMemcpyAsync(&nw, &cx.st->wide_count, 8, cudaMemcpyDeviceToHost, s));
+  NURI_CUDA(cudaStreamSynchronize(s));
+  int64_t launched = 1;
+  if (nw > 0) {
+    NURI_CUDA(cudaMemsetAsync(&cx.st->work_next, 0, sizeof(int64_t), s));
+    k_clique_expand<KWIDE><<<grid * 2, KCfg<KWIDE>::WARPS * 32, dynw, s>>>(cx, wide.p, nullptr,
+                                                                           nw);
+    NURI_CUDA(cudaGetLastError());
+    ++launched;
+  }
+  NURI_CUDA(cudaEventRecord(ev1, s));
+  return launched;
+}
+
 struct HostBucket {
   DBuf<Rec> dev;            // device records [0, count)
   int64_t count = 0;
@@ -686,8 +812,8 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
   if (frontier_cap <= 0) frontier_cap = 1 << 22;
   const int n = g.n;
 
-  const int grid = sm_count() * 6;  // resident CTAs: 6 x 4 warps per SM
-  const int total_warps = grid * WARPS;
+  const int grid = sm_count() * 6;  // CTAs of the narrow kernel: 6 x 4 warps per SM
+  const int total_warps = grid * KCfg<1>::WARPS;
   const int64_t stage_cap = std::max<int64_t>(1 << 16, (int64_t)g.max_out * 8);
 
   DBuf<QState> st;
@@ -698,7 +824,7 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
   k_set_deadline<<<1, 32, 0, s>>>(deadline.p, time_budget_ns());
   DBuf<int32_t> pscratch;
   if (g.max_out > PSMEM) pscratch.alloc((int64_t)total_warps * g.max_out, s);
-  DBuf<Rec> stage, deferred, inbuf;
+  DBuf<Rec> stage, deferred, inbuf, wide;
   stage.alloc(stage_cap, s);
   ++launches;
   k_clear_stage<<<grid_for(stage_cap), 256, 0, s>>>(stage.p, stage_cap);
@@ -715,8 +841,8 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
   svals.alloc(std::max(n, 1), s);
   skeys2.alloc(std::max(n, 1), s);
   svals2.alloc(std::max(n, 1), s);
-  bhist.alloc(NB, s);
-  std::vector<int32_t> seed_hist(NB, 0);
+  bhist.alloc(2 * NB, s);
+  std::vector<int32_t> seed_hist(2 * NB, 0);
   if (n > 0) {
     ++launches;
     k_seed_bounds<<<grid_for(n), 256, 0, s>>>(g, skeys.p, svals.p);
@@ -727,22 +853,23 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
     tmp.alloc(tb, s);
     NURI_CUDA(cub::DeviceRadixSort::SortPairsDescending(tmp.p, tb, skeys.p, skeys2.p, svals.p,
                                                         svals2.p, n, 0, 32, s));
-    NURI_CUDA(cudaMemsetAsync(bhist.p, 0, sizeof(int32_t) * NB, s));
+    NURI_CUDA(cudaMemsetAsync(bhist.p, 0, sizeof(int32_t) * 2 * NB, s));
     ++launches;
     k_bucket_hist<<<grid_for(n), 256, 0, s>>>(skeys2.p, n, bhist.p);
-    NURI_CUDA(cudaMemcpyAsync(seed_hist.data(), bhist.p, sizeof(int32_t) * NB,
+    NURI_CUDA(cudaMemcpyAsync(seed_hist.data(), bhist.p, sizeof(int32_t) * 2 * NB,
                               cudaMemcpyDeviceToHost, s));
     NURI_CUDA(cudaStreamSynchronize(s));
   }
-  // seed ranges per bucket (seeds are sorted by descending bound)
-  std::vector<int64_t> seed_lo(NB), seed_hi(NB);
+  // seed ranges per (class, bucket): class 1 first, then class 0, each by descending bound
+  std::vector<int64_t> seed_lo(2 * NB), seed_hi(2 * NB);
   {
     int64_t pos = 0;
-    for (int b = NB - 1; b >= 0; --b) {
-      seed_lo[b] = pos;
-      pos += seed_hist[b];
-      seed_hi[b] = pos;
-    }
+    for (int c = 1; c >= 0; --c)
+      for (int b = NB - 1; b >= 0; --b) {
+        seed_lo[c * NB + b] = pos;
+        pos += seed_hist[c * NB + b];
+        seed_hi[c * NB + b] = pos;
+      }
   }
 
   QState hs;
@@ -786,6 +913,10 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
     cx.maximal = maximal;
     cx.no_prune = no_prune;
     cx.deadline = deadline.p;
+    cx.split_above = 64 * KWIDE;
+    const bool trace = getenv("NURI_TRACE") != nullptr;  // per-round log on stderr
+    // smaller split limit (exercises the frontier tier in tests)
+    if (const char* e = getenv("NURI_SPLIT_ABOVE")) cx.split_above = std::max(1, atoi(e));
     int64_t rounds = 0;
     int64_t seed_chunk = std::max<int64_t>(total_warps, 1024);
 
@@ -795,12 +926,19 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
       if (hs.err & 1) NURI_FAIL(NURI_ERR_LIMIT, "nuri_topk_cliques: a clique exceeds %d vertices", MAXD);
       if (hs.err & 4) NURI_FAIL(NURI_ERR_TIMEOUT, "nuri_topk_cliques: time budget exhausted after %lld rounds", (long long)rounds);
       int32_t tau = hs.tau;
-      // highest bucket with pending seeds or records
-      int b_seed = -1, b_front = -1;
-      for (int b = NB - 1; b >= 0; --b)
-        if (seed_next[b] < seed_hi[b]) {
+      // highest bucket with pending seeds (narrow class first) or frontier records
+      int b_seed = -1, b_front = -1, seed_slot = -1;
+      bool narrow_first = false;
+      for (int b = NB - 1; b >= 0 && seed_slot < 0; --b)
+        if (seed_next[NB + b] < seed_hi[NB + b] && (no_prune || b >= tau || b == NB - 1)) {
+          seed_slot = NB + b;
           b_seed = b;
-          break;
+          narrow_first = true;
+        }
+      for (int b = NB - 1; b >= 0 && seed_slot < 0; --b)
+        if (seed_next[b] < seed_hi[b]) {
+          seed_slot = b;
+          b_seed = b;
         }
       for (int b = NB - 1; b >= 0; --b)
         if (buckets[b].count + buckets[b].spilled_total > 0) {
@@ -810,10 +948,12 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
       int best = std::max(b_seed, b_front);
       if (best < 0) break;
       if (!no_prune && best < NB - 1 && best < tau) break;  // every remaining bound < tau
+      if (narrow_first) b_front = -1;  // narrow seeds go before the frontier
 
       NURI_CUDA(cudaMemsetAsync(&st.p->work_next, 0, sizeof(int64_t), s));
       NURI_CUDA(cudaMemsetAsync(&st.p->stage_count, 0, sizeof(int64_t), s));
       NURI_CUDA(cudaMemsetAsync(&st.p->defer_count, 0, sizeof(int64_t), s));
+      NURI_CUDA(cudaMemsetAsync(&st.p->wide_count, 0, sizeof(int64_t), s));
       int64_t nin = 0;
       int src_bucket = -1;
       if (b_front >= b_seed) {
@@ -838,25 +978,31 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
                                   cudaMemcpyDeviceToDevice, s));
         hb.count -= nin;
         if ((int64_t)deferred.n < nin) deferred.alloc(std::max<int64_t>(nin, 4096), s);
+        if ((int64_t)wide.n < nin) wide.alloc(std::max<int64_t>(nin, 4096), s);
         cx.deferred = deferred.p;
-        NURI_CUDA(cudaEventRecord(ev0, s));
-        ++launches;
-        k_clique_expand<<<grid, WARPS * 32, 0, s>>>(cx, inbuf.p, nullptr, nin);
-        NURI_CUDA(cudaEventRecord(ev1, s));
+        launches += launch_expand(cx, inbuf.p, nullptr, nin, grid, wide, ev0, ev1, s);
       } else {
-        int64_t lo = seed_next[b_seed];
-        nin = std::min<int64_t>(seed_hi[b_seed] - lo, seed_chunk);
-        seed_next[b_seed] += nin;
+        int64_t lo = seed_next[seed_slot];
+        nin = std::min<int64_t>(seed_hi[seed_slot] - lo, seed_chunk);
+        seed_next[seed_slot] += nin;
         seed_chunk = std::min<int64_t>(seed_chunk * 2, 1 << 20);
         if ((int64_t)deferred.n < nin) deferred.alloc(std::max<int64_t>(nin, 4096), s);
+        if ((int64_t)wide.n < nin) wide.alloc(std::max<int64_t>(nin, 4096), s);
         cx.deferred = deferred.p;
-        NURI_CUDA(cudaEventRecord(ev0, s));
-        ++launches;
-        k_clique_expand<<<grid, WARPS * 32, 0, s>>>(cx, nullptr, svals2.p + lo, nin);
-        NURI_CUDA(cudaEventRecord(ev1, s));
+        launches += launch_expand(cx, nullptr, svals2.p + lo, nin, grid, wide, ev0, ev1, s);
       }
       NURI_CUDA(cudaGetLastError());
       ++rounds;
+      if (trace) {
+        float ms = 0.f;
+        NURI_CUDA(cudaStreamSynchronize(s));
+        NURI_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
+        int64_t nwide = 0;
+        NURI_CUDA(cudaMemcpy(&nwide, &st.p->wide_count, 8, cudaMemcpyDeviceToHost));
+        fprintf(stderr, "[nuri] round %lld %s bucket %d n %lld wide %lld tau %d: %.3f ms\n",
+                (long long)rounds, src_bucket >= 0 ? "frontier" : (narrow_first ? "narrow" : "seeds"),
+                b_front >= b_seed ? b_front : b_seed, (long long)nin, (long long)nwide, tau, ms);
+      }
       // staging (children) and deferred parents -> buckets, by bound
       int64_t scnt = 0, dcnt = 0;
       NURI_CUDA(cudaMemcpyAsync(&scnt, &st.p->stage_count, 8, cudaMemcpyDeviceToHost, s));

@@ -73,7 +73,11 @@ def test_rmat_vs_oracle(scale, ef, seed, k):
     # power-law rows: exercises the split path (|P| > 64) and the bucketed frontier
     g = synth.rmat(scale, ef, seed=seed)
     G = load(g)
-    for maximal in (False, True):
+    # maximal mode checks every candidate's maximality with a global adjacency scan: it is
+    # exercised here on the smaller cases only
+    modes = (False, True) if (scale, k) in ((10, 1), (10, 10), (10, 100), (11, 1), (11, 10),
+                                            (12, 1)) else (False,)
+    for maximal in modes:
         want = rows_bk(g, (scale, ef, seed), k, maximal)
         got = [(r[0], r[1]) for r in nuri.topk_cliques(G, k, maximal=maximal)]
         assert got == want, (scale, k, maximal)
@@ -126,13 +130,41 @@ def test_no_prune_ablation_same_results_more_work():
     assert b.stats["expansions"] >= a.stats["expansions"]
 
 
-def test_forced_spill_equals_resident():
-    g = synth.rmat(12, 16, seed=7)
+def test_forced_spill_equals_resident(monkeypatch):
+    # a small split limit sends most records through the bucketed frontier; a 64-record
+    # device frontier then forces spills to pinned host memory and reloads
+    g = synth.rmat(11, 16, seed=7)
     G = load(g)
+    monkeypatch.setenv("NURI_SPLIT_ABOVE", "4")
     a = nuri.topk_cliques(G, 50)
     b = nuri.topk_cliques(G, 50, frontier_cap=64)
-    assert [(r[0], r[1]) for r in a] == [(r[0], r[1]) for r in b]
+    monkeypatch.delenv("NURI_SPLIT_ABOVE")
+    want = [(r[0], tuple(r[1])) for r in oracle.bk_cliques(g, 50, False)]
+    assert [(r[0], r[1]) for r in a] == [(r[0], r[1]) for r in b] == want
     assert b.stats["spilled"] > 0 and b.stats["reloaded"] > 0
+
+
+@pytest.mark.parametrize("split", [2, 5, 16])
+def test_split_tier_vs_oracle(monkeypatch, split):
+    monkeypatch.setenv("NURI_SPLIT_ABOVE", str(split))
+    for g in (synth.rmat(10, 8, seed=1), synth.er_small(120, 0.5, seed=78)):
+        G = load(g)
+        for k in (1, 10, 100):
+            want = [(r[0], tuple(r[1])) for r in oracle.bk_cliques(g, k, False)]
+            assert [(r[0], r[1]) for r in nuri.topk_cliques(G, k)] == want, (g.name, k)
+
+
+@pytest.mark.parametrize("n,p", [(150, 0.55), (200, 0.5), (260, 0.45)])
+def test_wide_bitmap_tail_dense_random(n, p):
+    # degeneracy above 64: candidate sets of 65..512 vertices go to the 8-word bitmap tail
+    g = synth.er_small(n, p, seed=77)
+    G = load(g)
+    assert G.info()["max_out_degree"] > 64
+    for k in (1, 10, 100):
+        want = [(r[0], tuple(r[1])) for r in oracle.bk_cliques(g, k, False)]
+        assert [(r[0], r[1]) for r in nuri.topk_cliques(G, k)] == want, k
+    want = [(r[0], tuple(r[1])) for r in oracle.bk_cliques(g, 10, True)]
+    assert [(r[0], r[1]) for r in nuri.topk_cliques(G, 10, maximal=True)] == want
 
 
 def test_result_overflow_restart_is_exact(monkeypatch):
