@@ -147,6 +147,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--ref-budget", type=int, default=30_000_000)
+    ap.add_argument("--workload", default="headline", choices=["headline", "serving"])
+    ap.add_argument("--serving-graph", default="rmat22")
+    ap.add_argument("--requests", type=int, default=1000)
+    ap.add_argument("--calibrate", type=int, default=200)
+    ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--request-budget-ms", type=float, default=60000.0)
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -164,6 +170,14 @@ def main():
         dist.init_process_group("nccl")
     stream = torch.cuda.current_stream()
     sptr = stream.cuda_stream
+    if args.workload == "serving":
+        res = serving(args, nuri, torch, sptr)
+        line = {"metric": METRIC, "workload": "serving", "unit": "ms", "n_gpus": world,
+                "higher_is_better": False, "data": "synthetic (seeded R-MAT + Poisson arrivals)",
+                "dtype": "int32", "serving": res}
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
     g = synth.workload("chunglu1m")
     G = nuri.load_graph(g.n, g.src, g.dst, stream=sptr)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device="cuda")
@@ -266,6 +280,95 @@ def main():
 
 def _ms(r):
     return r.stats["device_ms"]
+
+
+def serving(args, nuri, torch, sptr):
+    """Open-loop serving on the resident R-MAT scale-22 graph: Poisson arrivals of a 50/50 mix
+    of top-k clique (k 1..100) and isomorphism (3..8 vertices, k 10..1000) requests at 0.5, 1
+    and 2 times the plain one-at-a-time throughput mu1 (calibrated on 200 requests)."""
+    import synth
+    g = synth.workload(args.serving_graph)
+    t0 = time.perf_counter()
+    G = nuri.load_graph(g.n, g.src, g.dst, labels=g.labels, weights=g.weights, index_hops=4,
+                        stream=sptr)
+    load_s = time.perf_counter() - t0
+    nuri.set_time_budget(args.request_budget_ms)
+
+    def run_alone(r):
+        if r["kind"] == "clique":
+            return nuri.topk_cliques(G, r["k"], stream=sptr)
+        return nuri.topk_iso(G, r["query"], r["k"], stream=sptr)
+
+    calib = synth.serving_requests(args.calibrate, rate=1.0, seed=100)
+    for r in calib[:5]:
+        run_alone(r)
+    t0 = time.perf_counter()
+    fails = 0
+    for r in calib:
+        try:
+            run_alone(r)
+        except nuri.NuriError:
+            fails += 1
+    mu1 = len(calib) / (time.perf_counter() - t0)
+    out = {"graph": args.serving_graph, "edges": G.info()["num_edges"], "load_s": load_s,
+           "mu1_req_per_s": mu1, "calibration_failures": fails, "slots": args.slots,
+           "requests_per_rate": args.requests, "rates": {}}
+    for i, f in enumerate((0.5, 1.0, 2.0)):
+        rate = f * mu1
+        reqs = synth.serving_requests(args.requests, rate=rate, seed=i)
+        srv = nuri.Server(G, slots=args.slots, max_batch=64)
+        tickets = [None] * len(reqs)
+        start = time.perf_counter()
+
+        def submitter():
+            for j, r in enumerate(reqs):
+                delay = start + r["t"] - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                tickets[j] = (srv.submit_cliques(r["k"]) if r["kind"] == "clique"
+                              else srv.submit_iso(r["query"], r["k"]))
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        lat, errs, done = [], 0, 0
+        pending = set()
+        j = 0
+        while done < len(reqs):
+            while j < len(reqs) and tickets[j] is not None:
+                pending.add(j)
+                j += 1
+            finished = []
+            for q in pending:
+                try:
+                    rr = srv.poll(tickets[q])
+                except nuri.NuriError:
+                    rr = ("error", None)
+                if rr is None:
+                    continue
+                finished.append(q)
+                if rr[0] == "error":
+                    errs += 1
+                else:
+                    # latency from the scheduled arrival (includes any submission delay)
+                    lat.append((time.perf_counter() - start - reqs[q]["t"]) * 1e3)
+            for q in finished:
+                pending.discard(q)
+            done += len(finished)
+            if not finished:
+                time.sleep(0.0005)
+        wall = time.perf_counter() - start
+        th.join()
+        st = srv.stats()
+        srv.close()
+        lat.sort()
+        out["rates"][f"{f}x"] = {
+            "offered_req_per_s": rate, "completed_req_per_s": len(reqs) / wall,
+            "p50_ms": lat[len(lat) // 2] if lat else None,
+            "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))] if lat else None,
+            "errors": errs, "iso_batches": st["iso_batches"],
+            "iso_requests": st["iso_batched_requests"]}
+    nuri.set_time_budget(0)
+    return out
 
 
 def extra_workloads(nuri, torch, sptr):

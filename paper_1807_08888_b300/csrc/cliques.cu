@@ -207,6 +207,22 @@ __device__ __forceinline__ bool any(const unsigned long long* X, int wa) {
   return a != 0;
 }
 
+// single-bit updates through unrolled predicated loops: the masks stay in registers
+// (an index computed at run time would move the whole array to local memory)
+template <int W>
+__device__ __forceinline__ void clear_bit(unsigned long long* X, int v) {
+#pragma unroll
+  for (int q = 0; q < W; ++q)
+    if (q == (v >> 6)) X[q] &= ~(1ull << (v & 63));
+}
+
+template <int W>
+__device__ __forceinline__ void set_bit(unsigned long long* X, int v) {
+#pragma unroll
+  for (int q = 0; q < W; ++q)
+    if (q == (v >> 6)) X[q] |= 1ull << (v & 63);
+}
+
 template <int W>
 __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
     k_clique_expand(Ctx cx, const Rec* __restrict__ in, const int32_t* __restrict__ seeds,
@@ -215,7 +231,10 @@ __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
   constexpr int BMW = 64 * W;   // candidates the bitmap tail handles
   __shared__ int32_t sP[NW][PSMEM];
   __shared__ int32_t sV[NW][MAXD];
-  extern __shared__ unsigned long long dynrows[];  // NW * BMW * W words: upper rows of P
+  __shared__ uint16_t sOrd[NW][BMW], sPos[NW][BMW], sCol[NW][BMW];
+  __shared__ int32_t sCnt[NW][BMW];
+  __shared__ int32_t sTot[NW], sNext[NW];
+  extern __shared__ unsigned long long dynrows[];  // NW * BMW * W words: adjacency rows of P
 
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
@@ -357,6 +376,11 @@ __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
 
     if (p <= lim) {
       // ================= bitmap tail: finish the whole subtree in this warp =================
+      // Colour-ordered branching (the MCQ/MCS scheme of exact maximum-clique search): a
+      // greedy colouring of the candidates P bounds the clique they can add by the number of
+      // colours; children are taken from the highest colour class down and every remaining
+      // child is pruned once |C| + colours(remaining) < tau.  Every clique is still produced
+      // exactly once: after a child v is explored, v leaves the candidates of its siblings.
       const int wa = (p + 63) >> 6;  // words in use
       int32_t* sp = sP[w];
       if (P != sp) {
@@ -364,13 +388,13 @@ __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
         __syncwarp();
       }
       const int32_t plast = sp[p - 1];
-      // row[i] = bits j > i with sp[j] in N+(sp[i])
+      for (int i = lane; i < p * W; i += 32) rows[i] = 0;
+      __syncwarp();
+      // symmetric adjacency of P: each out-row entry x of sp[i] found at index j sets (i, j)
+      // and (j, i)
       for (int i = 0; i < p; ++i) {
         int32_t v = sp[i];
         int64_t rb = g.ooff[v], re = g.ooff[v + 1];
-        unsigned long long bits[W];
-#pragma unroll
-        for (int q = 0; q < W; ++q) bits[q] = 0;
         int64_t scanned = 0;
         for (int64_t base = rb; base < re; base += 32) {
           int64_t t = base + lane;
@@ -378,194 +402,265 @@ __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
           if (x <= plast) {
             int j = lower_bound_dev(sp, i + 1, p, x);
             if (j < p && sp[j] == x) {
-#pragma unroll
-              for (int q = 0; q < W; ++q)
-                if ((j >> 6) == q) bits[q] |= 1ull << (j & 63);
+              atomicOr(rows + i * W + (j >> 6), 1ull << (j & 63));
+              atomicOr(rows + j * W + (i >> 6), 1ull << (i & 63));
             }
           }
           scanned += 32;
-          // rows are sorted: stop once the whole chunk is past the last candidate
-          if (__all_sync(FULL, x > plast)) break;
-        }
-#pragma unroll
-        for (int q = 0; q < W; ++q) {
-          if (q >= wa) break;
-          unsigned lo = __reduce_or_sync(FULL, (unsigned)bits[q]);
-          unsigned hi = __reduce_or_sync(FULL, (unsigned)(bits[q] >> 32));
-          if (lane == 0) rows[i * W + q] = ((unsigned long long)hi << 32) | lo;
+          if (__all_sync(FULL, x > plast)) break;  // rows are sorted
         }
         if (lane == 0) my_bytes += 4ull * (unsigned long long)(scanned < re - rb ? scanned : re - rb);
       }
       __syncwarp();
-      // Lane tasks: task j < p is the child node {P_j} alone; the other tasks are the
-      // subtrees rooted at the grandchildren {P_j, P_b} (b in row[j]), so a dense child's
-      // subtree is spread over many lanes.  Every node is visited by exactly one task.
-      int ntask = p;
-      for (int j = 0; j < p; ++j) ntask += popc<W>(rows + j * W, wa);
+      // record-level colouring (index order) and the order of the children by colour
+      uint16_t* ord = sOrd[w];   // vertices by ascending colour
+      uint16_t* pos = sPos[w];   // position of each vertex in ord
+      uint16_t* col = sCol[w];   // colour of each vertex (1-based)
+      if (lane == 0) {
+        unsigned long long left[W];
+#pragma unroll
+        for (int q = 0; q < W; ++q) left[q] = 0;
+        for (int i = 0; i < p; ++i) set_bit<W>(left, i);
+        int c = 0, o = 0;
+        while (any<W>(left, wa)) {
+          ++c;
+          unsigned long long cls[W];
+#pragma unroll
+          for (int q = 0; q < W; ++q) cls[q] = left[q];
+          int v;
+          while ((v = lowest<W>(cls, wa)) >= 0) {
+#pragma unroll
+            for (int q = 0; q < W; ++q) cls[q] &= ~rows[v * W + q];
+            clear_bit<W>(cls, v);
+            clear_bit<W>(left, v);
+            col[v] = (uint16_t)c;
+            pos[v] = (uint16_t)o;
+            ord[o++] = (uint16_t)v;
+          }
+        }
+      }
+      __syncwarp();
+      // Two-level lane tasks.  Children: ord[i] for i from p-1 down, with the candidates
+      // adjacent to it that come earlier in ord (P_i), the explored ones later in ord (X_i),
+      // and the bound |V| + colour(ord[i]).  Phase 1 visits every child node and counts the
+      // candidates of the viable children; phase 2 hands out, through a shared counter, one
+      // task per (child i, candidate j of P_i): the subtree rooted at {ord[i], j} whose
+      // candidates are the members of P_i after j (index order) adjacent to j.  Every clique
+      // of the record's subtree is visited by exactly one task.
       bool limit_hit = false, out_of_time = false;
       int32_t t_cache = ld_volatile(&cx.st->tau);
-      int tj = 0, tb = -1;  // (j, b) of the task with index tnext
-      int tnext = 0;
-      // per-lane DFS state: pick[d] = index in P added at depth d; for W == 1 the untried
-      // siblings of depth d are kept in stk[d], for wider masks they are recomputed from rows
-      uint16_t pick[BMW + 1];
-      unsigned long long stk[W == 1 ? BMW : 1];
-      for (int task = lane; task < ntask && !out_of_time; task += 32) {
-        int depth;
-        unsigned long long X[W];
-        if (task < p) {
-          depth = 0;
-          pick[0] = (uint16_t)task;
+      int32_t* cnt = sCnt[w];
+      auto child_sets = [&](int i, unsigned long long* Pi, unsigned long long* Xi) {
+        const int v0 = ord[i];
 #pragma unroll
-          for (int q = 0; q < W; ++q) X[q] = rows[task * W + q];
-        } else {
-          // walk the (j, b) enumeration forward to index `task`
-          if (tnext < p) {
-            tnext = p;
-            tj = 0;
-            while (!any<W>(rows + tj * W, wa)) ++tj;
-            tb = lowest<W>(rows + tj * W, wa);
-          }
-          while (tnext < task) {
-            // next set bit of row tj after tb, else the first bit of the next non-empty row
-            int nb = -1;
-            for (int q = (tb + 1) >> 6; q < wa && nb < 0; ++q) {
-              unsigned long long m = rows[tj * W + q];
-              if (q == ((tb + 1) >> 6)) m = ((tb + 1) & 63) ? (m & ~((1ull << ((tb + 1) & 63)) - 1)) : m;
-              if (m) nb = q * 64 + __ffsll((long long)m) - 1;
-            }
-            if (nb >= 0) {
-              tb = nb;
-            } else {
-              do {
-                ++tj;
-              } while (!any<W>(rows + tj * W, wa));
-              tb = lowest<W>(rows + tj * W, wa);
-            }
-            ++tnext;
-          }
-          depth = 1;
-          pick[0] = (uint16_t)tj;
-          pick[1] = (uint16_t)tb;
-#pragma unroll
-          for (int q = 0; q < W; ++q) X[q] = rows[tj * W + q] & rows[tb * W + q];
-          if (W == 1) stk[0] = 0;  // the siblings of this grandchild are other tasks
+        for (int q = 0; q < W; ++q) {
+          Pi[q] = 0;
+          Xi[q] = 0;
         }
-        const bool single = task < p;  // a child task visits its own node only
-        while (true) {
-          // node: record + pick[0..depth], candidates X
-          int size = nv + depth + 1;
-          ++my_exp;
-          if ((my_exp & 31) == 0) {
+        for (int u = 0; u < p; ++u) {
+          if ((rows[v0 * W + (u >> 6)] & (1ull << (u & 63))) == 0) continue;
+          if (pos[u] < i) set_bit<W>(Pi, u);
+          else set_bit<W>(Xi, u);
+        }
+      };
+      // ---- phase 1: the child nodes ----
+      for (int i = p - 1 - lane; i >= 0; i -= 32) {
+        const int v0 = ord[i];
+        cnt[i] = 0;
+        if (!cx.no_prune && nv + (int)col[v0] < t_cache) {
+          ++my_pruned;
+          continue;
+        }
+        unsigned long long Pi[W], Xi[W];
+        child_sets(i, Pi, Xi);
+        ++my_exp;
+        const int size = nv + 1;
+        if (size >= t_cache) {
+          bool rel = true;
+          if (cx.maximal) {
+            if (any<W>(Pi, wa) || any<W>(Xi, wa)) rel = false;
+            else {
+              int32_t C[MAXD];
+              for (int a = 0; a < nv; ++a) C[a] = sV[w][a];
+              C[nv] = sp[v0];
+              rel = is_maximal(g, C, size);
+            }
+          }
+          if (rel) {
+            int32_t pr = sp[v0];
+            add_result(cx, sV[w], nv, 1, &pr);
             t_cache = ld_volatile(&cx.st->tau);
-            if ((my_exp & 1023) == 0 && past_deadline(cx)) {
-              atomicOr(&cx.st->err, 4);
-              out_of_time = true;
-              break;
-            }
           }
-          int32_t t_now = t_cache;
-          int bnd = size + popc<W>(X, wa);
-          // a greedy colouring of the candidates bounds the clique they can add (a clique
-          // takes at most one vertex per colour class); tighter than |P| on dense candidates.
-          // Classes are built in index order, so the upper rows suffice: a vertex leaves the
-          // class being built as soon as a lower-index member is adjacent to it.
-          if (!cx.no_prune && bnd >= t_now && bnd - 1 > size) {
-            int colours = 0;
-            unsigned long long left[W];
+        }
+        if (any<W>(Pi, wa) && size >= MAXD) limit_hit = true;
+        else cnt[i] = popc<W>(Pi, wa);
+      }
+      __syncwarp();
+      if (lane == 0) {
+        int acc = 0;
+        for (int i = 0; i < p; ++i) {
+          int c = cnt[i];
+          cnt[i] = acc;  // exclusive prefix
+          acc += c;
+        }
+        sTot[w] = acc;
+        sNext[w] = 0;
+      }
+      __syncwarp();
+      const int ntask = sTot[w];
+      // per-lane DFS stack: the untried candidates (and, for maximality, the explored ones)
+      // of every level; pick[d] = index in P of the vertex added at depth d
+      unsigned long long stkP[MAXD][W];
+      unsigned long long stkX[MAXD][W];
+      uint16_t pick[MAXD + 1];
+      // ---- phase 2: grandchild subtrees, taken dynamically ----
+      while (!out_of_time) {
+        int t = atomicAdd(&sNext[w], 1);
+        if (t >= ntask) break;
+        // child i: the last index with cnt[i] <= t (cnt is non-decreasing)
+        int lo = 0, hi = p - 1;
+        while (lo < hi) {
+          int mid = (lo + hi + 1) >> 1;
+          if (cnt[mid] <= t) lo = mid;
+          else hi = mid - 1;
+        }
+        const int i = lo;
+        int r = t - cnt[i];  // the r-th candidate of P_i in index order
+        unsigned long long Pn[W], Xn[W];
+        child_sets(i, Pn, Xn);
+        int j = -1;
 #pragma unroll
-            for (int q = 0; q < W; ++q) left[q] = X[q];
-            while (any<W>(left, wa) && size + colours < t_now) {
-              ++colours;
-              unsigned long long cls[W];
-#pragma unroll
-              for (int q = 0; q < W; ++q) cls[q] = left[q];
-              int v;
-              while ((v = lowest<W>(cls, wa)) >= 0) {
-#pragma unroll
-                for (int q = 0; q < W; ++q) cls[q] &= ~rows[v * W + q];
-                cls[v >> 6] &= ~(1ull << (v & 63));
-                left[v >> 6] &= ~(1ull << (v & 63));
-              }
-            }
-            if (any<W>(left, wa)) colours += 1;  // stopped early: the bound already reaches tau
-            bnd = size + colours;
+        for (int q = 0; q < W; ++q) {
+          if (j >= 0 || q >= wa) continue;
+          int c = __popcll(Pn[q]);
+          if (r < c) {
+            unsigned long long m = Pn[q];
+            for (int s2 = 0; s2 < r; ++s2) m &= m - 1;
+            j = q * 64 + __ffsll((long long)m) - 1;
+          } else {
+            r -= c;
           }
-          bool expand_node = !single;
-          if (!cx.no_prune && bnd < t_now) {
-            ++my_pruned;
-            expand_node = false;
-          } else if (size >= t_now) {
-            bool rel = true;
-            int32_t pick_ranks[MAXD];
-            for (int d = 0; d <= depth; ++d) pick_ranks[d] = sp[pick[d]];
-            if (cx.maximal) {
-              if (any<W>(X, wa)) rel = false;
-              else {
-                int32_t C[MAXD];
-                for (int i = 0; i < nv; ++i) C[i] = sV[w][i];
-                for (int d = 0; d <= depth; ++d) C[nv + d] = pick_ranks[d];
-                rel = is_maximal(g, C, size);
-              }
-            }
-            if (rel) {
-              add_result(cx, sV[w], nv, depth + 1, pick_ranks);
+        }
+        // the grandchild {ord[i], j}: candidates of P_i after j adjacent to j; the members of
+        // P_i before j join the explored set
+        unsigned long long below[W];
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+          if (q < (j >> 6)) below[q] = ~0ull;
+          else if (q == (j >> 6)) below[q] = (j & 63) ? ((1ull << (j & 63)) - 1) : 0ull;
+          else below[q] = 0ull;
+        }
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+          unsigned long long pj = Pn[q];
+          Xn[q] = (Xn[q] | (pj & below[q])) & rows[j * W + q];
+          Pn[q] = pj & ~below[q] & rows[j * W + q];
+        }
+        clear_bit<W>(Pn, j);
+        int depth = 1;
+        pick[0] = (uint16_t)ord[i];
+        pick[1] = (uint16_t)j;
+        // visit the node (record + picks[0..depth], candidates Pn, explored Xn), then branch
+        bool visit = true;
+        while (true) {
+          int size = nv + depth + 1;
+          if (visit) {
+            ++my_exp;
+            if ((my_exp & 31) == 0) {
               t_cache = ld_volatile(&cx.st->tau);
+              if ((my_exp & 1023) == 0 && past_deadline(cx)) {
+                atomicOr(&cx.st->err, 4);
+                out_of_time = true;
+                break;
+              }
             }
-          }
-          if (expand_node && any<W>(X, wa) && size >= MAXD) {
-            limit_hit = true;
-            expand_node = false;
-          }
-          if (expand_node && any<W>(X, wa)) {
-            // descend into the lowest candidate; the others are its later siblings
-            int b = lowest<W>(X, wa);
-            if (W == 1) stk[depth] = X[0] & (X[0] - 1);
-            ++depth;
-            pick[depth] = (uint16_t)b;
-#pragma unroll
-            for (int q = 0; q < W; ++q) X[q] &= rows[b * W + q];
-            X[b >> 6] &= ~(1ull << (b & 63));
-            continue;
-          }
-          if (single) break;
-          // back up to the next sibling that can still reach tau (depth 1 is the task root)
-          bool done = false;
-          while (true) {
-            if (depth <= 1) {
-              done = true;
-              break;
+            if (size >= t_cache) {
+              bool rel = true;
+              if (cx.maximal) {
+                if (any<W>(Pn, wa) || any<W>(Xn, wa)) rel = false;
+                else {
+                  int32_t C[MAXD];
+                  for (int a = 0; a < nv; ++a) C[a] = sV[w][a];
+                  for (int d = 0; d <= depth; ++d) C[nv + d] = sp[pick[d]];
+                  rel = is_maximal(g, C, size);
+                }
+              }
+              if (rel) {
+                int32_t pr[MAXD];
+                for (int d = 0; d <= depth; ++d) pr[d] = sp[pick[d]];
+                add_result(cx, sV[w], nv, depth + 1, pr);
+                t_cache = ld_volatile(&cx.st->tau);
+              }
             }
-            // untried siblings of the node at `depth`: candidates of its parent after it
-            unsigned long long rest[W];
-            if (W == 1) {
-              rest[0] = stk[depth - 1];
+            visit = false;
+          }
+          // branch: colour the untried candidates; stop when they cannot reach tau
+          int branch = -1;
+          if (any<W>(Pn, wa)) {
+            if (size >= MAXD) {
+              limit_hit = true;
+            } else if (cx.no_prune) {
+              branch = lowest<W>(Pn, wa);
             } else {
+              unsigned long long left[W];
 #pragma unroll
-              for (int q = 0; q < W; ++q) rest[q] = rows[pick[0] * W + q];
-              for (int d = 1; d < depth; ++d)
+              for (int q = 0; q < W; ++q) left[q] = Pn[q];
+              int colours = 0, last_first = -1;
+              while (any<W>(left, wa) && size + colours < t_cache) {
+                ++colours;
+                unsigned long long cls[W];
 #pragma unroll
-                for (int q = 0; q < W; ++q) rest[q] &= rows[pick[d] * W + q];
-              int c = pick[depth];  // clear every bit <= c
+                for (int q = 0; q < W; ++q) cls[q] = left[q];
+                int v;
+                last_first = -1;
+                while ((v = lowest<W>(cls, wa)) >= 0) {
+                  if (last_first < 0) last_first = v;
+#pragma unroll
+                  for (int q = 0; q < W; ++q) cls[q] &= ~rows[v * W + q];
+                  clear_bit<W>(cls, v);
+                  clear_bit<W>(left, v);
+                }
+              }
+              if (any<W>(left, wa)) branch = lowest<W>(left, wa);  // a high-colour vertex
+              else if (size + colours >= t_cache) branch = last_first;
+              else ++my_pruned;
+            }
+          }
+          if (branch >= 0) {
+            // child: add `branch`; it leaves the untried candidates of this node
+            {
+              unsigned long long sp2[W], sx2[W];
 #pragma unroll
               for (int q = 0; q < W; ++q) {
-                if (q < (c >> 6)) rest[q] = 0;
-                else if (q == (c >> 6)) rest[q] &= ((c & 63) == 63) ? 0ull : ~((2ull << (c & 63)) - 1);
+                sp2[q] = Pn[q];
+                sx2[q] = Xn[q];
+              }
+              clear_bit<W>(sp2, branch);
+              if (cx.maximal) set_bit<W>(sx2, branch);
+#pragma unroll
+              for (int q = 0; q < W; ++q) {
+                stkP[depth][q] = sp2[q];
+                stkX[depth][q] = sx2[q];
               }
             }
-            int parent_size = nv + depth;  // size of the node whose children are iterated
-            if (!any<W>(rest, wa) || (!cx.no_prune && parent_size + popc<W>(rest, wa) < t_cache)) {
-              --depth;
-              continue;
-            }
-            int b = lowest<W>(rest, wa);
-            if (W == 1) stk[depth - 1] = rest[0] & (rest[0] - 1);
-            pick[depth] = (uint16_t)b;
 #pragma unroll
-            for (int q = 0; q < W; ++q) X[q] = rest[q] & rows[b * W + q];
-            break;
+            for (int q = 0; q < W; ++q) {
+              Pn[q] &= rows[branch * W + q];
+              Xn[q] &= rows[branch * W + q];
+            }
+            ++depth;
+            pick[depth] = (uint16_t)branch;
+            visit = true;
+            continue;
           }
-          if (done) break;
+          // done with this node: back to its parent's remaining candidates
+          if (depth == 1) break;
+          --depth;
+#pragma unroll
+          for (int q = 0; q < W; ++q) {
+            Pn[q] = stkP[depth][q];
+            Xn[q] = stkX[depth][q];
+          }
         }
       }
       if (limit_hit) atomicOr(&cx.st->err, 1);
