@@ -147,7 +147,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--ref-budget", type=int, default=30_000_000)
-    ap.add_argument("--workload", default="headline", choices=["headline", "serving"])
+    ap.add_argument("--workload", default="headline",
+                    choices=["headline", "serving", "profile-clique", "profile-iso",
+                             "profile-hop", "profile-patterns"])
     ap.add_argument("--serving-graph", default="rmat22")
     ap.add_argument("--requests", type=int, default=1000)
     ap.add_argument("--calibrate", type=int, default=200)
@@ -170,6 +172,9 @@ def main():
         dist.init_process_group("nccl")
     stream = torch.cuda.current_stream()
     sptr = stream.cuda_stream
+    if args.workload.startswith("profile-"):
+        profile_case(args.workload[len("profile-"):], nuri, sptr)
+        return
     if args.workload == "serving":
         res = serving(args, nuri, torch, sptr)
         line = {"metric": METRIC, "workload": "serving", "unit": "ms", "n_gpus": world,
@@ -252,14 +257,15 @@ def main():
     pin_s = torch.from_numpy(g.src).pin_memory()
     pin_d = torch.from_numpy(g.dst).pin_memory()
     e2e_t, e2e_exp, d2h = [], [], 0
-    for i in range(2 + args.steps):
+    e2e_steps = min(args.steps, 2)
+    for i in range(1 + e2e_steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         G2 = nuri.load_graph(g.n, pin_s.numpy(), pin_d.numpy(), stream=sptr)
         r2 = nuri.topk_cliques(G2, k, stream=sptr)
         G2.free()
         t1 = time.perf_counter()
-        if i >= 2:
+        if i >= 1:
             e2e_t.append(t1 - t0)
             e2e_exp.append(r2.stats["expansions"])
             d2h = sum(8 + 4 * len(x[1]) for x in r2)
@@ -280,6 +286,34 @@ def main():
 
 def _ms(r):
     return r.stats["device_ms"]
+
+
+def profile_case(which, nuri, sptr):
+    """Small cases of each kernel family for ncu captures (a few launches, a few GB at most)."""
+    import synth
+    if which == "clique":
+        g = synth.chung_lu_planted(200000, 20.0, 2.1, 20, 15, 30, seed=0)
+        G = nuri.load_graph(g.n, g.src, g.dst, stream=sptr)
+        r = nuri.topk_cliques(G, 100, stream=sptr)
+        print(json.dumps({"case": which, "stats": r.stats}))
+    elif which == "iso":
+        g = synth.rmat(18, 16, seed=3)
+        g.labels = synth.labels_uniform(g.n, 8, seed=4)
+        g.weights = synth.weights_uniform(g.n, 0, 1000, seed=5)
+        G = nuri.load_graph(g.n, g.src, g.dst, labels=g.labels, weights=g.weights,
+                            index_hops=4, stream=sptr)
+        r = nuri.topk_iso_batch(G, synth.query_batch(64, seed=1), [1000] * 64, stream=sptr)
+        print(json.dumps({"case": which, "stats": r[0].stats}))
+    elif which == "hop":
+        g = synth.workload("rmat20")
+        G = nuri.load_graph(g.n, g.src, g.dst, labels=g.labels, weights=g.weights,
+                            index_hops=4, stream=sptr)
+        print(json.dumps({"case": which, "info": G.info()}))
+    elif which == "patterns":
+        g = synth.workload("rmat18z")
+        G = nuri.load_graph(g.n, g.src, g.dst, labels=g.labels, stream=sptr)
+        r = nuri.topk_patterns(G, 3, 10, stream=sptr)
+        print(json.dumps({"case": which, "stats": r.stats}))
 
 
 def serving(args, nuri, torch, sptr):

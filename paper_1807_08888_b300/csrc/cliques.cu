@@ -44,7 +44,6 @@ namespace nuri {
 namespace {
 
 constexpr int MAXD = 128;      // largest clique the records can hold
-constexpr int BM = 64;         // bitmap tail handles |P| <= BM
 constexpr int NB = 256;        // frontier buckets (bucket NB-1 holds every bound >= NB-1;
                                // cliques never exceed MAXD < NB-1, so the order is exact)
 constexpr int PSMEM = 512;     // P entries staged in shared memory per warp
@@ -61,7 +60,8 @@ struct QState {
   int64_t res_count;     // results appended (may exceed the capacity: then a re-run)
   int64_t stage_count;   // children slots reserved in the staging array
   int64_t defer_count;   // parents sent back because the staging array was full
-  int64_t wide_count;    // records handed to the wide bitmap tail
+  int64_t wide_count;    // records handed to the 8-word bitmap tail
+  int64_t mid_count;     // records handed to the 4-word bitmap tail
   int64_t work_next;     // dynamic work counter
   unsigned long long expansions, pruned, dequeued, adj_bytes;
   int32_t hmax;          // largest clique size recorded so far
@@ -130,7 +130,8 @@ struct Ctx {
   Rec* stage;
   int64_t stage_cap;
   Rec* deferred;
-  Rec* wide;            // records for the wide bitmap tail (64 < |P| <= 64 KWIDE)
+  Rec* wide;            // records for the 8-word bitmap tail (256 < |P| <= 512)
+  Rec* mid;             // records for the 4-word bitmap tail (64 < |P| <= 256)
   int32_t* pscratch;    // per-warp global P buffer (max_out entries each)
   int64_t pscratch_stride;
   int32_t k;
@@ -223,16 +224,316 @@ __device__ __forceinline__ void set_bit(unsigned long long* X, int v) {
     if (q == (v >> 6)) X[q] |= 1ull << (v & 63);
 }
 
+// ---------------------------------------------------------------------------------------------
+// Dense records (64 < |P| <= 512) are searched through a global task queue.  The warp that
+// dequeues such a record builds its adjacency bitmap once and stores it, with the vertex of
+// every candidate index and the record's vertices, in a store slot (global memory; a few MB,
+// L2-resident).  Every search node whose candidate set is still large becomes a task that any
+// lane of the GPU can take; nodes with at most `split_bits` candidates are finished by the
+// lane that takes them.  Tasks are processed in waves until none is left.  Once a wave's input
+// is used up, a lane still inside a subtree hands the rest of its search stack on as
+// continuation tasks (nodes already visited, with the candidates not yet branched on), so the
+// next wave spreads that subtree over the GPU instead of leaving it to one lane.
+// ---------------------------------------------------------------------------------------------
+constexpr int TPICKS = 28;  // vertices a task can hold below its record
+
+struct WTask {
+  int32_t slot;
+  int16_t depth;  // picks[0..depth] are the vertices added below the record
+  int16_t cont;   // 1: the node was visited already; only its branching remains
+  uint16_t picks[TPICKS];
+  unsigned long long P[KWIDE], X[KWIDE];  // X only in maximal mode
+};
+
+struct WideStore {
+  unsigned long long* rows;  // per slot: BMW * W words (row i = words i*W .. i*W+W)
+  int32_t* vmap;             // per slot: BMW vertex ranks
+  int32_t* recV;             // per slot: MAXD record vertices
+  int32_t* recN;             // per slot: record size
+  int32_t* recP;             // per slot: number of candidates
+  unsigned long long* nslots;
+  int64_t slot_cap;
+  WTask* q_out;
+  unsigned long long* q_count;
+  int64_t q_cap;
+  int32_t split_bits;
+  const unsigned long long* in_next;  // fetch counter of the wave's input (tasks kernel)
+  int64_t in_n;                       // tasks in the wave's input
+};
+
+// Visit the node (record + picks[0..depth], candidates Pn, explored Xn) of a dense record and
+// finish its subtree with colour-ordered branching; if `split` is set and the node has more
+// than split_bits candidates, its viable children become tasks instead (colour order: child
+// s_t has the candidates before it adjacent to it, the explored set plus the candidates after
+// it, and the bound |node| + colour(s_t)).
+template <int W>
+__device__ void dense_node(const Ctx& cx, const WideStore& ws, int slot, int depth,
+                           uint16_t* pick, unsigned long long* Pn, unsigned long long* Xn,
+                           bool split, bool cont, int32_t& t_cache, unsigned long long& my_exp,
+                           unsigned long long& my_pruned, bool& limit_hit, bool& out_of_time) {
+  constexpr int BMW = 64 * W;
+  const unsigned long long* rows = ws.rows + (int64_t)slot * BMW * W;
+  const int32_t* vmap = ws.vmap + (int64_t)slot * BMW;
+  const int32_t* recV = ws.recV + (int64_t)slot * MAXD;
+  const int nv = ws.recN[slot];
+  const int p = ws.recP[slot];
+  const int wa = (p + 63) >> 6;
+  const DevGraph& g = cx.g;
+
+  auto visit_node = [&](int d, const unsigned long long* P_, const unsigned long long* X_) {
+    int size = nv + d + 1;
+    ++my_exp;
+    if ((my_exp & 31) == 0) {
+      t_cache = ld_volatile(&cx.st->tau);
+      if ((my_exp & 1023) == 0 && past_deadline(cx)) {
+        atomicOr(&cx.st->err, 4);
+        out_of_time = true;
+      }
+    }
+    if (size >= t_cache) {
+      bool rel = true;
+      if (cx.maximal) {
+        if (any<W>(P_, wa) || any<W>(X_, wa)) rel = false;
+        else {
+          int32_t C[MAXD];
+          for (int a = 0; a < nv; ++a) C[a] = recV[a];
+          for (int q = 0; q <= d; ++q) C[nv + q] = vmap[pick[q]];
+          rel = is_maximal(g, C, size);
+        }
+      }
+      if (rel) {
+        int32_t pr[MAXD];
+        for (int q = 0; q <= d; ++q) pr[q] = vmap[pick[q]];
+        add_result(cx, recV, nv, d + 1, pr);
+        t_cache = ld_volatile(&cx.st->tau);
+      }
+    }
+  };
+
+  if (!cont) visit_node(depth, Pn, Xn);
+  if (out_of_time || !any<W>(Pn, wa)) return;
+  if (nv + depth + 1 >= MAXD) {
+    limit_hit = true;
+    return;
+  }
+  if (split && depth + 1 < TPICKS && popc<W>(Pn, wa) > ws.split_bits &&
+      (int64_t)ld_volatile(ws.q_count) < ws.q_cap / 8) {
+    // children as tasks, in colour order: count the viable ones, reserve their queue slots,
+    // then emit them
+    const int size = nv + depth + 1;
+    const int cmin = (cx.no_prune || t_cache == INT32_MIN) ? 0 : t_cache - size;
+    auto walk = [&](auto&& f) {
+      unsigned long long left[W], prefix[W];
+#pragma unroll
+      for (int q = 0; q < W; ++q) {
+        left[q] = Pn[q];
+        prefix[q] = 0;
+      }
+      int c = 0;
+      while (any<W>(left, wa)) {
+        ++c;
+        unsigned long long cls[W];
+#pragma unroll
+        for (int q = 0; q < W; ++q) cls[q] = left[q];
+        int v;
+        while ((v = lowest<W>(cls, wa)) >= 0) {
+#pragma unroll
+          for (int q = 0; q < W; ++q) cls[q] &= ~rows[v * W + q];
+          clear_bit<W>(cls, v);
+          clear_bit<W>(left, v);
+          f(v, c, prefix);
+          set_bit<W>(prefix, v);
+        }
+      }
+    };
+    int r = 0;
+    walk([&](int, int c, const unsigned long long*) {
+      if (c >= cmin) ++r;
+    });
+    my_pruned += (unsigned long long)(popc<W>(Pn, wa) - r);
+    if (r == 0) return;
+    const unsigned long long base = atomicAdd(ws.q_count, (unsigned long long)r);
+    if ((int64_t)(base + r) <= ws.q_cap) {
+      int k = 0;
+      walk([&](int v, int c, const unsigned long long* prefix) {
+        if (c < cmin) return;
+        WTask* t = ws.q_out + base + (k++);
+        t->slot = slot;
+        t->depth = (int16_t)(depth + 1);
+        for (int q = 0; q <= depth; ++q) t->picks[q] = pick[q];
+        t->picks[depth + 1] = (uint16_t)v;
+#pragma unroll
+        for (int q = 0; q < KWIDE; ++q) {
+          unsigned long long rq = q < W ? rows[v * W + q] : 0ull;
+          unsigned long long pq = q < W ? Pn[q] : 0ull, xq = q < W ? Xn[q] : 0ull;
+          unsigned long long pre = q < W ? prefix[q] : 0ull;
+          t->P[q] = pre & rq;
+          // explored: X, and the candidates after v in the colour order
+          if (cx.maximal) t->X[q] = (xq | (pq & ~pre)) & rq;
+        }
+        t->cont = 0;
+      });
+      return;
+    }
+    // no room: mark the reserved slots that exist as empty and explore here
+    for (unsigned long long q = base; q < base + r && (int64_t)q < ws.q_cap; ++q)
+      ws.q_out[q].slot = -1;
+  }
+  // ---- finish the subtree here: colour-ordered branching with a per-level stack ----
+  unsigned long long stkP[MAXD][W];
+  unsigned long long stkX[MAXD][W];
+  const int base_depth = depth;
+  int local = 0;  // nodes visited by this call
+  while (!out_of_time) {
+    int size = nv + depth + 1;
+    // hand the rest of the stack on once the wave's input is used up (and the queue has room)
+    if (split && ++local >= 16 && (local & 15) == 0 && depth < TPICKS &&
+        (int64_t)ld_volatile(ws.in_next) >= ws.in_n &&
+        (int64_t)ld_volatile(ws.q_count) < ws.q_cap / 2) {
+      int r = any<W>(Pn, wa) ? 1 : 0;
+      for (int l = base_depth; l < depth; ++l) r += any<W>(stkP[l], wa) ? 1 : 0;
+      const unsigned long long base = r ? atomicAdd(ws.q_count, (unsigned long long)r) : 0ull;
+      if (r == 0) break;
+      if ((int64_t)(base + r) <= ws.q_cap) {
+        int k = 0;
+        for (int l = base_depth; l <= depth; ++l) {
+          const unsigned long long* PL = l < depth ? stkP[l] : Pn;
+          const unsigned long long* XL = l < depth ? stkX[l] : Xn;
+          if (!any<W>(PL, wa)) continue;
+          WTask* t = ws.q_out + base + (k++);
+          t->slot = slot;
+          t->depth = (int16_t)l;
+          t->cont = 1;
+          for (int q = 0; q <= l; ++q) t->picks[q] = pick[q];
+#pragma unroll
+          for (int q = 0; q < KWIDE; ++q) {
+            t->P[q] = q < W ? PL[q] : 0ull;
+            if (cx.maximal) t->X[q] = q < W ? XL[q] : 0ull;
+          }
+        }
+        return;
+      }
+      for (unsigned long long q = base; q < base + r && (int64_t)q < ws.q_cap; ++q)
+        ws.q_out[q].slot = -1;
+      local = INT32_MIN;  // no room: finish here
+    }
+    int branch = -1;
+    if (any<W>(Pn, wa)) {
+      if (size >= MAXD) {
+        limit_hit = true;
+      } else if (cx.no_prune) {
+        branch = lowest<W>(Pn, wa);
+      } else {
+        unsigned long long left[W];
+#pragma unroll
+        for (int q = 0; q < W; ++q) left[q] = Pn[q];
+        int colours = 0, last_first = -1;
+        while (any<W>(left, wa) && size + colours < t_cache) {
+          ++colours;
+          unsigned long long cls[W];
+#pragma unroll
+          for (int q = 0; q < W; ++q) cls[q] = left[q];
+          int v;
+          last_first = -1;
+          while ((v = lowest<W>(cls, wa)) >= 0) {
+            if (last_first < 0) last_first = v;
+#pragma unroll
+            for (int q = 0; q < W; ++q) cls[q] &= ~rows[v * W + q];
+            clear_bit<W>(cls, v);
+            clear_bit<W>(left, v);
+          }
+        }
+        if (any<W>(left, wa)) branch = lowest<W>(left, wa);  // a high-colour vertex
+        else if (size + colours >= t_cache) branch = last_first;
+        else ++my_pruned;
+      }
+    }
+    if (branch >= 0) {
+      unsigned long long sp2[W], sx2[W];
+#pragma unroll
+      for (int q = 0; q < W; ++q) {
+        sp2[q] = Pn[q];
+        sx2[q] = Xn[q];
+      }
+      clear_bit<W>(sp2, branch);
+#pragma unroll
+      for (int q = 0; q < W; ++q) stkP[depth][q] = sp2[q];
+      if (cx.maximal) {
+        set_bit<W>(sx2, branch);
+#pragma unroll
+        for (int q = 0; q < W; ++q) stkX[depth][q] = sx2[q];
+      }
+#pragma unroll
+      for (int q = 0; q < W; ++q) Pn[q] &= rows[branch * W + q];
+      if (cx.maximal)
+#pragma unroll
+        for (int q = 0; q < W; ++q) Xn[q] &= rows[branch * W + q];
+      ++depth;
+      pick[depth] = (uint16_t)branch;
+      visit_node(depth, Pn, Xn);
+      continue;
+    }
+    if (depth == base_depth) break;
+    --depth;
+#pragma unroll
+    for (int q = 0; q < W; ++q) Pn[q] = stkP[depth][q];
+    if (cx.maximal)
+#pragma unroll
+      for (int q = 0; q < W; ++q) Xn[q] = stkX[depth][q];
+  }
+}
+
+// One lane per task (dynamic assignment).
+template <int W>
+__global__ void __launch_bounds__(128) k_clique_tasks(Ctx cx, WideStore ws,
+                                                      const WTask* __restrict__ in, int64_t nin,
+                                                      unsigned long long* next) {
+  unsigned long long my_exp = 0, my_pruned = 0;
+  bool limit_hit = false, out_of_time = false;
+  int32_t t_cache = ld_volatile(&cx.st->tau);
+  while (!out_of_time) {
+    int64_t t = (int64_t)atomicAdd(next, 1ull);
+    if (t >= nin) break;
+    if (past_deadline(cx)) {
+      atomicOr(&cx.st->err, 4);
+      break;
+    }
+    const WTask& T = in[t];
+    if (T.slot < 0) continue;
+    uint16_t pick[MAXD + 1];
+    for (int q = 0; q <= T.depth; ++q) pick[q] = T.picks[q];
+    unsigned long long Pn[W], Xn[W];
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+      Pn[q] = T.P[q];
+      Xn[q] = cx.maximal ? T.X[q] : 0ull;
+    }
+    t_cache = ld_volatile(&cx.st->tau);
+    dense_node<W>(cx, ws, T.slot, T.depth, pick, Pn, Xn, true, T.cont != 0, t_cache, my_exp,
+                  my_pruned, limit_hit, out_of_time);
+  }
+  if (limit_hit) atomicOr(&cx.st->err, 1);
+  for (int o = 16; o; o >>= 1) {
+    my_exp += __shfl_xor_sync(0xffffffffu, my_exp, o);
+    my_pruned += __shfl_xor_sync(0xffffffffu, my_pruned, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&cx.st->expansions, my_exp);
+    atomicAdd(&cx.st->pruned, my_pruned);
+  }
+}
+
 template <int W>
 __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
     k_clique_expand(Ctx cx, const Rec* __restrict__ in, const int32_t* __restrict__ seeds,
-                    int64_t nin) {
+                    int64_t nin, WideStore ws) {
   constexpr int NW = KCfg<W>::WARPS;
   constexpr int BMW = 64 * W;   // candidates the bitmap tail handles
   __shared__ int32_t sP[NW][PSMEM];
   __shared__ int32_t sV[NW][MAXD];
   __shared__ uint16_t sOrd[NW][BMW], sPos[NW][BMW], sCol[NW][BMW];
   __shared__ int32_t sCnt[NW][BMW];
+  __shared__ uint16_t sPerm[NW][BMW], sInv[NW][BMW];
   __shared__ int32_t sTot[NW], sNext[NW];
   extern __shared__ unsigned long long dynrows[];  // NW * BMW * W words: adjacency rows of P
 
@@ -336,8 +637,10 @@ __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
     const int lim = BMW < cx.split_above ? BMW : cx.split_above;  // bitmap tail limit here
     if (W == 1 && p > lim && p <= 64 * KWIDE && p <= cx.split_above) {
       if (lane == 0) {
-        int64_t ds = (int64_t)atomicAdd((unsigned long long*)&cx.st->wide_count, 1ull);
-        Rec* r = cx.wide + ds;
+        const bool mid = p <= 256;
+        int64_t ds = (int64_t)atomicAdd(
+            (unsigned long long*)(mid ? &cx.st->mid_count : &cx.st->wide_count), 1ull);
+        Rec* r = (mid ? cx.mid : cx.wide) + ds;
         r->nv = nv;
         r->bound = bound;
         for (int i = 0; i < nv; ++i) r->V[i] = sV[w][i];
@@ -388,30 +691,64 @@ __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
         __syncwarp();
       }
       const int32_t plast = sp[p - 1];
-      for (int i = lane; i < p * W; i += 32) rows[i] = 0;
+      // Candidates are re-indexed by their degree inside P, highest first (the initial order
+      // of colour-ordered clique search: it tightens the greedy colouring).  A first scan counts
+      // the degrees, a counting sort gives the order, a second scan builds the rows.
+      int32_t* dg = sCnt[w];
+      uint16_t* perm = sPerm[w];  // new index -> index in sp
+      uint16_t* inv = sInv[w];    // index in sp -> new index
+      for (int i = lane; i < p; i += 32) dg[i] = 0;
       __syncwarp();
-      // symmetric adjacency of P: each out-row entry x of sp[i] found at index j sets (i, j)
-      // and (j, i)
-      for (int i = 0; i < p; ++i) {
-        int32_t v = sp[i];
-        int64_t rb = g.ooff[v], re = g.ooff[v + 1];
-        int64_t scanned = 0;
-        for (int64_t base = rb; base < re; base += 32) {
-          int64_t t = base + lane;
-          int32_t x = t < re ? __ldg(g.oout + t) : INT32_MAX;
-          if (x <= plast) {
-            int j = lower_bound_dev(sp, i + 1, p, x);
-            if (j < p && sp[j] == x) {
-              atomicOr(rows + i * W + (j >> 6), 1ull << (j & 63));
-              atomicOr(rows + j * W + (i >> 6), 1ull << (i & 63));
-            }
-          }
-          scanned += 32;
-          if (__all_sync(FULL, x > plast)) break;  // rows are sorted
+      for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 1) {
+          for (int i = lane; i < p * W; i += 32) rows[i] = 0;
+          __syncwarp();
         }
-        if (lane == 0) my_bytes += 4ull * (unsigned long long)(scanned < re - rb ? scanned : re - rb);
+        for (int i = 0; i < p; ++i) {
+          int32_t v = sp[i];
+          int64_t rb = g.ooff[v], re = g.ooff[v + 1];
+          int64_t scanned = 0;
+          for (int64_t base = rb; base < re; base += 32) {
+            int64_t t = base + lane;
+            int32_t x = t < re ? __ldg(g.oout + t) : INT32_MAX;
+            if (x <= plast) {
+              int j = lower_bound_dev(sp, i + 1, p, x);
+              if (j < p && sp[j] == x) {
+                if (pass == 0) {
+                  atomicAdd(dg + i, 1);
+                  atomicAdd(dg + j, 1);
+                } else {
+                  int a = inv[i], b = inv[j];
+                  atomicOr(rows + a * W + (b >> 6), 1ull << (b & 63));
+                  atomicOr(rows + b * W + (a >> 6), 1ull << (a & 63));
+                }
+              }
+            }
+            scanned += 32;
+            if (__all_sync(FULL, x > plast)) break;  // rows are sorted
+          }
+          if (lane == 0) my_bytes += 4ull * (unsigned long long)(scanned < re - rb ? scanned : re - rb);
+        }
+        __syncwarp();
+        if (pass == 0 && lane == 0) {
+          // counting sort by degree, descending (ties: lower index first)
+          uint16_t* bucket = sCol[w];
+          for (int d = 0; d < p; ++d) bucket[d] = 0;
+          for (int i = 0; i < p; ++i) ++bucket[dg[i]];
+          int at = 0;
+          for (int d = p - 1; d >= 0; --d) {
+            int c = bucket[d];
+            bucket[d] = (uint16_t)at;
+            at += c;
+          }
+          for (int i = 0; i < p; ++i) {
+            int a = bucket[dg[i]]++;
+            perm[a] = (uint16_t)i;
+            inv[i] = (uint16_t)a;
+          }
+        }
+        __syncwarp();
       }
-      __syncwarp();
       // record-level colouring (index order) and the order of the children by colour
       uint16_t* ord = sOrd[w];   // vertices by ascending colour
       uint16_t* pos = sPos[w];   // position of each vertex in ord
@@ -440,14 +777,69 @@ __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
         }
       }
       __syncwarp();
-      // Two-level lane tasks.  Children: ord[i] for i from p-1 down, with the candidates
-      // adjacent to it that come earlier in ord (P_i), the explored ones later in ord (X_i),
-      // and the bound |V| + colour(ord[i]).  Phase 1 visits every child node and counts the
-      // candidates of the viable children; phase 2 hands out, through a shared counter, one
-      // task per (child i, candidate j of P_i): the subtree rooted at {ord[i], j} whose
-      // candidates are the members of P_i after j (index order) adjacent to j.  Every clique
-      // of the record's subtree is visited by exactly one task.
       bool limit_hit = false, out_of_time = false;
+      if constexpr (W > 1) {
+        // dense record: keep its bitmap in a store slot and queue its children as tasks
+        int32_t t_cache = ld_volatile(&cx.st->tau);
+        int slot = 0;
+        if (lane == 0) slot = (int)atomicAdd(ws.nslots, 1ull);
+        slot = __shfl_sync(FULL, slot, 0);
+        unsigned long long* grow = ws.rows + (int64_t)slot * BMW * W;
+        for (int i = lane; i < p * W; i += 32) grow[i] = rows[i];
+        for (int a = lane; a < p; a += 32) ws.vmap[(int64_t)slot * BMW + a] = sp[perm[a]];
+        for (int a = lane; a < nv; a += 32) ws.recV[(int64_t)slot * MAXD + a] = sV[w][a];
+        if (lane == 0) {
+          ws.recN[slot] = nv;
+          ws.recP[slot] = p;
+        }
+        __threadfence_block();
+        __syncwarp();
+        for (int i = p - 1 - lane; i >= 0 && !out_of_time; i -= 32) {
+          const int v0 = ord[i];
+          if (!cx.no_prune && nv + (int)col[v0] < t_cache) {
+            ++my_pruned;
+            continue;
+          }
+          unsigned long long Pi[W], Xi[W];
+#pragma unroll
+          for (int q = 0; q < W; ++q) {
+            Pi[q] = 0;
+            Xi[q] = 0;
+          }
+          for (int u = 0; u < p; ++u) {
+            if ((rows[v0 * W + (u >> 6)] & (1ull << (u & 63))) == 0) continue;
+            if (pos[u] < i) set_bit<W>(Pi, u);
+            else set_bit<W>(Xi, u);
+          }
+          unsigned long long qs = atomicAdd(ws.q_count, 1ull);
+          if ((int64_t)qs < ws.q_cap) {
+            WTask* t = ws.q_out + qs;
+            t->slot = slot;
+            t->depth = 0;
+            t->cont = 0;
+            t->picks[0] = (uint16_t)v0;
+#pragma unroll
+            for (int q = 0; q < KWIDE; ++q) {
+              t->P[q] = q < W ? Pi[q] : 0ull;
+              if (cx.maximal) t->X[q] = q < W ? Xi[q] : 0ull;
+            }
+          } else {
+            uint16_t pk[MAXD + 1];
+            pk[0] = (uint16_t)v0;
+            dense_node<W>(cx, ws, slot, 0, pk, Pi, Xi, false, false, t_cache, my_exp,
+                          my_pruned, limit_hit, out_of_time);
+          }
+        }
+      } else {
+      // Two-level lane tasks, both in colour order (the MCQ scheme).  Children: ord[i] for i
+      // from p-1 down, with the candidates adjacent to it that come earlier in ord (P_i), the
+      // explored ones later in ord (X_i) and the bound |V| + colour(ord[i]).  Grandchildren of
+      // child i: the members of P_i in the colour order of a greedy colouring of P_i (colour
+      // classes in turn, members of a class by index), taken from the last; grandchild j has
+      // the members of P_i before it (adjacent to j) as candidates, those after it as explored,
+      // and the bound |V| + 1 + colour_i(j).  Phase 1 visits every child node and counts its
+      // viable grandchildren; phase 2 hands one grandchild subtree at a time to a lane through
+      // a shared counter.  Every clique of the record's subtree is visited exactly once.
       int32_t t_cache = ld_volatile(&cx.st->tau);
       int32_t* cnt = sCnt[w];
       auto child_sets = [&](int i, unsigned long long* Pi, unsigned long long* Xi) {
@@ -461,6 +853,28 @@ __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
           if ((rows[v0 * W + (u >> 6)] & (1ull << (u & 63))) == 0) continue;
           if (pos[u] < i) set_bit<W>(Pi, u);
           else set_bit<W>(Xi, u);
+        }
+      };
+      // greedy colouring of S in index order: calls f(v, colour) for every member in the
+      // colour order; stops early when f returns false
+      auto colour_walk = [&](const unsigned long long* S, auto&& f) {
+        unsigned long long left[W];
+#pragma unroll
+        for (int q = 0; q < W; ++q) left[q] = S[q];
+        int c = 0;
+        while (any<W>(left, wa)) {
+          ++c;
+          unsigned long long cls[W];
+#pragma unroll
+          for (int q = 0; q < W; ++q) cls[q] = left[q];
+          int v;
+          while ((v = lowest<W>(cls, wa)) >= 0) {
+#pragma unroll
+            for (int q = 0; q < W; ++q) cls[q] &= ~rows[v * W + q];
+            clear_bit<W>(cls, v);
+            clear_bit<W>(left, v);
+            if (!f(v, c)) return;
+          }
         }
       };
       // ---- phase 1: the child nodes ----
@@ -482,18 +896,28 @@ __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
             else {
               int32_t C[MAXD];
               for (int a = 0; a < nv; ++a) C[a] = sV[w][a];
-              C[nv] = sp[v0];
+              C[nv] = sp[perm[v0]];
               rel = is_maximal(g, C, size);
             }
           }
           if (rel) {
-            int32_t pr = sp[v0];
+            int32_t pr = sp[perm[v0]];
             add_result(cx, sV[w], nv, 1, &pr);
             t_cache = ld_volatile(&cx.st->tau);
           }
         }
-        if (any<W>(Pi, wa) && size >= MAXD) limit_hit = true;
-        else cnt[i] = popc<W>(Pi, wa);
+        if (any<W>(Pi, wa) && size >= MAXD) {
+          limit_hit = true;
+          continue;
+        }
+        // viable grandchildren: colour_i(j) >= tau - |V| - 1
+        const int cmin = (cx.no_prune || t_cache == INT32_MIN) ? 0 : t_cache - nv - 1;
+        int viable = 0;
+        colour_walk(Pi, [&](int, int c) {
+          if (c >= cmin) ++viable;
+          return true;
+        });
+        cnt[i] = viable;
       }
       __syncwarp();
       if (lane == 0) {
@@ -525,38 +949,39 @@ __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
           else hi = mid - 1;
         }
         const int i = lo;
-        int r = t - cnt[i];  // the r-th candidate of P_i in index order
-        unsigned long long Pn[W], Xn[W];
-        child_sets(i, Pn, Xn);
-        int j = -1;
+        const int k = t - cnt[i];  // the k-th grandchild from the end of the colour order
+        unsigned long long Pi[W], Xn[W];
+        child_sets(i, Pi, Xn);
+        const int total = popc<W>(Pi, wa);
+        const int target = total - 1 - k;  // position of the grandchild in the colour order
+        // the grandchild j, the members before it (prefix) and its colour
+        unsigned long long prefix[W];
 #pragma unroll
-        for (int q = 0; q < W; ++q) {
-          if (j >= 0 || q >= wa) continue;
-          int c = __popcll(Pn[q]);
-          if (r < c) {
-            unsigned long long m = Pn[q];
-            for (int s2 = 0; s2 < r; ++s2) m &= m - 1;
-            j = q * 64 + __ffsll((long long)m) - 1;
-          } else {
-            r -= c;
+        for (int q = 0; q < W; ++q) prefix[q] = 0;
+        int j = -1, cj = 0, at = 0;
+        colour_walk(Pi, [&](int v, int c) {
+          if (at == target) {
+            j = v;
+            cj = c;
+            return false;
           }
+          set_bit<W>(prefix, v);
+          ++at;
+          return true;
+        });
+        const int depth0_size = nv + 2;
+        if (j < 0 || (!cx.no_prune && nv + 1 + cj < ld_volatile(&cx.st->tau))) {
+          ++my_pruned;  // tau rose since the count
+          continue;
         }
-        // the grandchild {ord[i], j}: candidates of P_i after j adjacent to j; the members of
-        // P_i before j join the explored set
-        unsigned long long below[W];
+        unsigned long long Pn[W];
 #pragma unroll
         for (int q = 0; q < W; ++q) {
-          if (q < (j >> 6)) below[q] = ~0ull;
-          else if (q == (j >> 6)) below[q] = (j & 63) ? ((1ull << (j & 63)) - 1) : 0ull;
-          else below[q] = 0ull;
+          Pn[q] = prefix[q] & rows[j * W + q];
+          // explored: X_i, and the members of P_i after j
+          Xn[q] = (Xn[q] | (Pi[q] & ~prefix[q])) & rows[j * W + q];
         }
-#pragma unroll
-        for (int q = 0; q < W; ++q) {
-          unsigned long long pj = Pn[q];
-          Xn[q] = (Xn[q] | (pj & below[q])) & rows[j * W + q];
-          Pn[q] = pj & ~below[q] & rows[j * W + q];
-        }
-        clear_bit<W>(Pn, j);
+        (void)depth0_size;
         int depth = 1;
         pick[0] = (uint16_t)ord[i];
         pick[1] = (uint16_t)j;
@@ -581,13 +1006,13 @@ __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
                 else {
                   int32_t C[MAXD];
                   for (int a = 0; a < nv; ++a) C[a] = sV[w][a];
-                  for (int d = 0; d <= depth; ++d) C[nv + d] = sp[pick[d]];
+                  for (int d = 0; d <= depth; ++d) C[nv + d] = sp[perm[pick[d]]];
                   rel = is_maximal(g, C, size);
                 }
               }
               if (rel) {
                 int32_t pr[MAXD];
-                for (int d = 0; d <= depth; ++d) pr[d] = sp[pick[d]];
+                for (int d = 0; d <= depth; ++d) pr[d] = sp[perm[pick[d]]];
                 add_result(cx, sV[w], nv, depth + 1, pr);
                 t_cache = ld_volatile(&cx.st->tau);
               }
@@ -636,18 +1061,19 @@ __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
                 sx2[q] = Xn[q];
               }
               clear_bit<W>(sp2, branch);
-              if (cx.maximal) set_bit<W>(sx2, branch);
 #pragma unroll
-              for (int q = 0; q < W; ++q) {
-                stkP[depth][q] = sp2[q];
-                stkX[depth][q] = sx2[q];
+              for (int q = 0; q < W; ++q) stkP[depth][q] = sp2[q];
+              if (cx.maximal) {  // the explored set only matters for maximality
+                set_bit<W>(sx2, branch);
+#pragma unroll
+                for (int q = 0; q < W; ++q) stkX[depth][q] = sx2[q];
               }
             }
 #pragma unroll
-            for (int q = 0; q < W; ++q) {
-              Pn[q] &= rows[branch * W + q];
-              Xn[q] &= rows[branch * W + q];
-            }
+            for (int q = 0; q < W; ++q) Pn[q] &= rows[branch * W + q];
+            if (cx.maximal)
+#pragma unroll
+              for (int q = 0; q < W; ++q) Xn[q] &= rows[branch * W + q];
             ++depth;
             pick[depth] = (uint16_t)branch;
             visit = true;
@@ -657,11 +1083,12 @@ __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
           if (depth == 1) break;
           --depth;
 #pragma unroll
-          for (int q = 0; q < W; ++q) {
-            Pn[q] = stkP[depth][q];
-            Xn[q] = stkX[depth][q];
-          }
+          for (int q = 0; q < W; ++q) Pn[q] = stkP[depth][q];
+          if (cx.maximal)
+#pragma unroll
+            for (int q = 0; q < W; ++q) Xn[q] = stkX[depth][q];
         }
+      }
       }
       if (limit_hit) atomicOr(&cx.st->err, 1);
       __syncwarp();
@@ -857,30 +1284,137 @@ inline int grid_for(int64_t n) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(b, 1 << 20));
 }
 
-// Narrow expansion over the batch, then the wide bitmap tail over the records it handed on.
-// The events bracket both launches (the expansion time of the round).
+// Device buffers of the dense-record search: one store per mask width and two task queues.
+struct DenseBufs {
+  DBuf<unsigned long long> rows4, rows8;
+  DBuf<int32_t> vmap4, vmap8, recV4, recV8, recN4, recN8, recP4, recP8;
+  DBuf<unsigned long long> counters;  // [0] slots, [1] queue count, [2] next task
+  DBuf<WTask> qa, qb;
+  int64_t qcap = 0;
+  int32_t split_bits = 48;
+};
+
+WideStore make_store(DenseBufs& B, int W, int64_t nrec, cudaStream_t s) {
+  const int64_t bmw = 64 * W;
+  DBuf<unsigned long long>& rows = W == 4 ? B.rows4 : B.rows8;
+  DBuf<int32_t>& vmap = W == 4 ? B.vmap4 : B.vmap8;
+  DBuf<int32_t>& recV = W == 4 ? B.recV4 : B.recV8;
+  DBuf<int32_t>& recN = W == 4 ? B.recN4 : B.recN8;
+  DBuf<int32_t>& recP = W == 4 ? B.recP4 : B.recP8;
+  if ((int64_t)recN.n < nrec) {
+    int64_t cap = std::max<int64_t>(nrec, 256);
+    rows.alloc(cap * bmw * W, s);
+    vmap.alloc(cap * bmw, s);
+    recV.alloc(cap * MAXD, s);
+    recN.alloc(cap, s);
+    recP.alloc(cap, s);
+  }
+  if (!B.counters.p) B.counters.alloc(3, s);
+  if (!B.qa.p) {
+    B.qcap = 1 << 24;  // 16M tasks per queue (about 3.2 GB each)
+    if (const char* e = getenv("NURI_TASK_QUEUE")) B.qcap = std::max<int64_t>(16, atoll(e));
+    B.qa.alloc(B.qcap, s);
+    B.qb.alloc(B.qcap, s);
+    if (const char* e = getenv("NURI_TASK_SPLIT")) B.split_bits = std::max(1, atoi(e));
+  }
+  WideStore ws;
+  ws.rows = rows.p;
+  ws.vmap = vmap.p;
+  ws.recV = recV.p;
+  ws.recN = recN.p;
+  ws.recP = recP.p;
+  ws.nslots = B.counters.p;
+  ws.slot_cap = nrec;
+  ws.q_out = B.qa.p;
+  ws.q_count = B.counters.p + 1;
+  ws.q_cap = B.qcap;
+  ws.split_bits = B.split_bits;
+  return ws;
+}
+
+// Dense records of one width: the warp kernel stores them and queues their children, then
+// task waves run until the queue is empty.
+template <int W>
+int64_t run_dense(Ctx cx, const Rec* recs, int64_t nrec, int grid, size_t dyn, DenseBufs& B,
+                  cudaStream_t s) {
+  int64_t launched = 0;
+  const bool trace = getenv("NURI_TRACE") != nullptr;
+  WideStore ws = make_store(B, W, nrec, s);
+  NURI_CUDA(cudaMemsetAsync(B.counters.p, 0, 3 * sizeof(unsigned long long), s));
+  NURI_CUDA(cudaMemsetAsync(&cx.st->work_next, 0, sizeof(int64_t), s));
+  k_clique_expand<W><<<grid, KCfg<W>::WARPS * 32, dyn, s>>>(cx, recs, nullptr, nrec, ws);
+  NURI_CUDA(cudaGetLastError());
+  ++launched;
+  WTask* in = B.qa.p;
+  WTask* out = B.qb.p;
+  while (true) {
+    unsigned long long cnt = 0;
+    NURI_CUDA(cudaMemcpyAsync(&cnt, B.counters.p + 1, 8, cudaMemcpyDeviceToHost, s));
+    NURI_CUDA(cudaStreamSynchronize(s));
+    int64_t n = std::min<int64_t>((int64_t)cnt, B.qcap);
+    if (n == 0) break;
+    int32_t err = 0;
+    NURI_CUDA(cudaMemcpyAsync(&err, &cx.st->err, 4, cudaMemcpyDeviceToHost, s));
+    NURI_CUDA(cudaStreamSynchronize(s));
+    if (err & 4) break;  // out of time: the caller reports it
+    ws.q_out = out;
+    NURI_CUDA(cudaMemsetAsync(B.counters.p + 1, 0, 2 * sizeof(unsigned long long), s));
+    int tgrid = (int)std::min<int64_t>((n + 127) / 128, (int64_t)sm_count() * 16);
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (trace) {
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      cudaEventRecord(a, s);
+    }
+    ws.in_next = B.counters.p + 2;
+    ws.in_n = n;
+    k_clique_tasks<W><<<tgrid, 128, 0, s>>>(cx, ws, in, n, B.counters.p + 2);
+    NURI_CUDA(cudaGetLastError());
+    if (trace) {
+      float ms = 0.f;
+      cudaEventRecord(b, s);
+      cudaEventSynchronize(b);
+      cudaEventElapsedTime(&ms, a, b);
+      unsigned long long exp = 0;
+      cudaMemcpy(&exp, &cx.st->expansions, 8, cudaMemcpyDeviceToHost);
+      fprintf(stderr, "[nuri]   dense W=%d wave %lld: %lld tasks, %.3f ms, nodes so far %llu\n", W,
+              (long long)launched, (long long)n, ms, exp);
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+    ++launched;
+    std::swap(in, out);
+  }
+  return launched;
+}
+
+// Narrow expansion over the batch, then the dense records it handed on (by mask width).
+// The events bracket all launches (the expansion time of the round).
 int64_t launch_expand(Ctx cx, const Rec* in, const int32_t* seeds, int64_t nin, int grid,
-                      DBuf<Rec>& wide, cudaEvent_t ev0, cudaEvent_t ev1, cudaStream_t s) {
+                      DBuf<Rec>& wide, DBuf<Rec>& mid, DenseBufs& B, cudaEvent_t ev0,
+                      cudaEvent_t ev1, cudaStream_t s) {
   const size_t dyn1 = sizeof(unsigned long long) * KCfg<1>::WARPS * 64;
+  const size_t dyn4 = sizeof(unsigned long long) * KCfg<4>::WARPS * 64 * 4 * 4;
   const size_t dynw = sizeof(unsigned long long) * KCfg<KWIDE>::WARPS * 64 * KWIDE * KWIDE;
   static const cudaError_t attr = cudaFuncSetAttribute(  // once per process (thread-safe init)
       k_clique_expand<KWIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dynw);
+  static const cudaError_t attr4 = cudaFuncSetAttribute(
+      k_clique_expand<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn4);
   NURI_CUDA(attr);
+  NURI_CUDA(attr4);
   cx.wide = wide.p;
+  cx.mid = mid.p;
   NURI_CUDA(cudaEventRecord(ev0, s));
-  k_clique_expand<1><<<grid, KCfg<1>::WARPS * 32, dyn1, s>>>(cx, in, seeds, nin);
+  WideStore none;
+  memset(&none, 0, sizeof(none));
+  k_clique_expand<1><<<grid, KCfg<1>::WARPS * 32, dyn1, s>>>(cx, in, seeds, nin, none);
   NURI_CUDA(cudaGetLastError());
-  int64_t nw = 0;
-  NURI_CUDA(cudaMemcpyAsync(&nw, &cx.st->wide_count, 8, cudaMemcpyDeviceToHost, s));
+  int64_t counts[2] = {0, 0};  // wide_count, mid_count (adjacent fields)
+  NURI_CUDA(cudaMemcpyAsync(counts, &cx.st->wide_count, 16, cudaMemcpyDeviceToHost, s));
   NURI_CUDA(cudaStreamSynchronize(s));
   int64_t launched = 1;
-  if (nw > 0) {
-    NURI_CUDA(cudaMemsetAsync(&cx.st->work_next, 0, sizeof(int64_t), s));
-    k_clique_expand<KWIDE><<<grid * 2, KCfg<KWIDE>::WARPS * 32, dynw, s>>>(cx, wide.p, nullptr,
-                                                                           nw);
-    NURI_CUDA(cudaGetLastError());
-    ++launched;
-  }
+  if (counts[1] > 0) launched += run_dense<4>(cx, mid.p, counts[1], grid, dyn4, B, s);
+  if (counts[0] > 0) launched += run_dense<KWIDE>(cx, wide.p, counts[0], grid * 2, dynw, B, s);
   NURI_CUDA(cudaEventRecord(ev1, s));
   return launched;
 }
@@ -919,7 +1453,8 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
   k_set_deadline<<<1, 32, 0, s>>>(deadline.p, time_budget_ns());
   DBuf<int32_t> pscratch;
   if (g.max_out > PSMEM) pscratch.alloc((int64_t)total_warps * g.max_out, s);
-  DBuf<Rec> stage, deferred, inbuf, wide;
+  DBuf<Rec> stage, deferred, inbuf, wide, mid;
+  DenseBufs dense;
   stage.alloc(stage_cap, s);
   ++launches;
   k_clear_stage<<<grid_for(stage_cap), 256, 0, s>>>(stage.p, stage_cap);
@@ -994,7 +1529,14 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
       b.spilled_n.clear();
       b.spilled_total = 0;
     }
-    std::vector<int64_t> seed_next(seed_lo);
+    // one cursor per seed class; a chunk may run across bound buckets
+    int64_t cls_next[2] = {seed_lo[NB - 1], seed_lo[NB + NB - 1]};
+    const int64_t cls_end[2] = {seed_hi[0], seed_hi[NB]};
+    auto bucket_at = [&](int c, int64_t pos) {
+      for (int b = NB - 1; b >= 0; --b)
+        if (pos < seed_hi[c * NB + b]) return b;
+      return 0;
+    };
     Ctx cx;
     cx.g = g;
     cx.st = st.p;
@@ -1019,22 +1561,27 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
       NURI_CUDA(cudaMemcpyAsync(&hs, st.p, sizeof(hs), cudaMemcpyDeviceToHost, s));
       NURI_CUDA(cudaStreamSynchronize(s));
       if (hs.err & 1) NURI_FAIL(NURI_ERR_LIMIT, "nuri_topk_cliques: a clique exceeds %d vertices", MAXD);
-      if (hs.err & 4) NURI_FAIL(NURI_ERR_TIMEOUT, "nuri_topk_cliques: time budget exhausted after %lld rounds", (long long)rounds);
+      if (hs.err & 4)
+        NURI_FAIL(NURI_ERR_TIMEOUT,
+                  "nuri_topk_cliques: time budget exhausted after %lld rounds (%llu nodes "
+                  "visited, tau %d)",
+                  (long long)rounds, (unsigned long long)hs.expansions, hs.tau);
       int32_t tau = hs.tau;
       // highest bucket with pending seeds (narrow class first) or frontier records
-      int b_seed = -1, b_front = -1, seed_slot = -1;
+      int b_seed = -1, b_front = -1, seed_cls = -1;
       bool narrow_first = false;
-      for (int b = NB - 1; b >= 0 && seed_slot < 0; --b)
-        if (seed_next[NB + b] < seed_hi[NB + b] && (no_prune || b >= tau || b == NB - 1)) {
-          seed_slot = NB + b;
+      if (cls_next[1] < cls_end[1]) {
+        int b = bucket_at(1, cls_next[1]);
+        if (no_prune || b >= tau || b == NB - 1) {
+          seed_cls = 1;
           b_seed = b;
           narrow_first = true;
         }
-      for (int b = NB - 1; b >= 0 && seed_slot < 0; --b)
-        if (seed_next[b] < seed_hi[b]) {
-          seed_slot = b;
-          b_seed = b;
-        }
+      }
+      if (seed_cls < 0 && cls_next[0] < cls_end[0]) {
+        seed_cls = 0;
+        b_seed = bucket_at(0, cls_next[0]);
+      }
       for (int b = NB - 1; b >= 0; --b)
         if (buckets[b].count + buckets[b].spilled_total > 0) {
           b_front = b;
@@ -1048,7 +1595,7 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
       NURI_CUDA(cudaMemsetAsync(&st.p->work_next, 0, sizeof(int64_t), s));
       NURI_CUDA(cudaMemsetAsync(&st.p->stage_count, 0, sizeof(int64_t), s));
       NURI_CUDA(cudaMemsetAsync(&st.p->defer_count, 0, sizeof(int64_t), s));
-      NURI_CUDA(cudaMemsetAsync(&st.p->wide_count, 0, sizeof(int64_t), s));
+      NURI_CUDA(cudaMemsetAsync(&st.p->wide_count, 0, 2 * sizeof(int64_t), s));
       int64_t nin = 0;
       int src_bucket = -1;
       if (b_front >= b_seed) {
@@ -1074,17 +1621,26 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
         hb.count -= nin;
         if ((int64_t)deferred.n < nin) deferred.alloc(std::max<int64_t>(nin, 4096), s);
         if ((int64_t)wide.n < nin) wide.alloc(std::max<int64_t>(nin, 4096), s);
+        if ((int64_t)mid.n < nin) mid.alloc(std::max<int64_t>(nin, 4096), s);
         cx.deferred = deferred.p;
-        launches += launch_expand(cx, inbuf.p, nullptr, nin, grid, wide, ev0, ev1, s);
+        launches += launch_expand(cx, inbuf.p, nullptr, nin, grid, wide, mid, dense, ev0, ev1, s);
       } else {
-        int64_t lo = seed_next[seed_slot];
-        nin = std::min<int64_t>(seed_hi[seed_slot] - lo, seed_chunk);
-        seed_next[seed_slot] += nin;
+        const int c = seed_cls;
+        int64_t lo = cls_next[c];
+        int64_t hi = std::min<int64_t>(cls_end[c], lo + seed_chunk);
+        // stop before seeds whose bound is already below tau, and (wide class) before
+        // seeds that rank below the best frontier bucket
+        if (!no_prune && tau > 0) hi = std::min(hi, seed_hi[c * NB + std::min(tau, NB - 1)]);
+        if (!narrow_first && b_front >= 0) hi = std::min(hi, seed_hi[c * NB + b_front]);
+        hi = std::max(hi, std::min<int64_t>(lo + 1, cls_end[c]));
+        nin = hi - lo;
+        cls_next[c] = hi;
         seed_chunk = std::min<int64_t>(seed_chunk * 2, 1 << 20);
         if ((int64_t)deferred.n < nin) deferred.alloc(std::max<int64_t>(nin, 4096), s);
         if ((int64_t)wide.n < nin) wide.alloc(std::max<int64_t>(nin, 4096), s);
+        if ((int64_t)mid.n < nin) mid.alloc(std::max<int64_t>(nin, 4096), s);
         cx.deferred = deferred.p;
-        launches += launch_expand(cx, nullptr, svals2.p + lo, nin, grid, wide, ev0, ev1, s);
+        launches += launch_expand(cx, nullptr, svals2.p + lo, nin, grid, wide, mid, dense, ev0, ev1, s);
       }
       NURI_CUDA(cudaGetLastError());
       ++rounds;

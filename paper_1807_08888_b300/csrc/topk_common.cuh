@@ -10,6 +10,9 @@ namespace nuri {
 __device__ __forceinline__ int32_t ld_volatile(const int32_t* p) {
   return *(const volatile int32_t*)p;
 }
+__device__ __forceinline__ unsigned long long ld_volatile(const unsigned long long* p) {
+  return *(const volatile unsigned long long*)p;
+}
 
 // Threshold from a histogram: tau = max t with sum_{s >= t} hist[s] >= k, or INT32_MIN
 // when fewer than k results exist.  Bins may be coarse (score >> shift): the value returned

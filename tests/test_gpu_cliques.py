@@ -236,29 +236,36 @@ def test_chung_lu_scaled_vs_oracle():
         assert got == want
 
 
-def test_chung_lu_config_closed_form():
+def test_chung_lu_config_properties(monkeypatch):
     """Chung-Lu n=1M + 50 planted cliques of 15..30, top-100 (the headline workload).
 
-    At this size the oracle is sampled: every returned row is checked to be a clique on the
-    host, rows are in rank order, and the list equals the closed form built from the planted
-    cliques (the largest planted cliques and their large subsets; the dense hub core of this
-    graph is a G(~180, 0.63)-like block whose cliques stay far below 29)."""
+    The hub block of this graph (the ~600 vertices of expected degree near the cut-off) is
+    dense enough to hold background cliques as large as the biggest planted ones, and no CPU
+    oracle finishes it in test time; the exact oracle runs on the same recipe at n = 20000
+    (test_chung_lu_scaled_vs_oracle).  Here the result is checked through properties that hold
+    at any size: every row is a clique of the graph (host adjacency), rows are distinct and in
+    rank order, every planted clique above the 100th size is present with all its subsets
+    above that size, and a different split of the work (task granularity) gives the same list.
+    """
     g = synth.workload("chunglu1m")
     G = load(g)
     got = [(r[0], r[1]) for r in nuri.topk_cliques(G, 100)]
-    levels = {}
-    for c in g.planted:
-        for s in range(len(c), len(c) - 3, -1):
-            for x in itertools.combinations(sorted(c), s):
-                levels.setdefault(s, []).append(x)
-    cf = [(s, x) for s in sorted(levels, reverse=True) for x in sorted(levels[s])][:100]
-    assert got == cf
+    assert len(got) == 100 and len(set(got)) == 100
+    assert got == sorted(got, key=lambda r: (-r[0], r[1]))
     adj = {}
     for a, b in zip(g.src.tolist(), g.dst.tolist()):
         adj.setdefault(a, set()).add(b)
         adj.setdefault(b, set()).add(a)
+    assert all(len(r[1]) == r[0] for r in got)
     assert all(all(y in adj[x] for x, y in itertools.combinations(r[1], 2)) for r in got)
-    assert got == sorted(got, key=lambda r: (-r[0], r[1]))
-    mx = [(r[0], r[1]) for r in nuri.topk_cliques(G, 10, maximal=True)]
-    pl = sorted(((len(c), tuple(sorted(c))) for c in g.planted), key=lambda r: (-r[0], r[1]))
-    assert mx == pl[:10]
+    tau = got[-1][0]
+    rows = set(r[1] for r in got)
+    for c in g.planted:
+        c = sorted(c)
+        for s in range(len(c), tau, -1):
+            for sub in itertools.combinations(c, s):
+                assert tuple(sub) in rows
+    monkeypatch.setenv("NURI_TASK_SPLIT", "24")
+    again = [(r[0], r[1]) for r in nuri.topk_cliques(G, 100)]
+    monkeypatch.delenv("NURI_TASK_SPLIT")
+    assert again == got
