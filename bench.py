@@ -41,6 +41,19 @@ def peaks():
         return 6400.0, "fallback"
 
 
+def alu_peak_gops():
+    """Peak rate of 64-bit bitmap word operations (AND / AND-NOT of an adjacency-row word into
+    a candidate mask): 148 SMs x 64 32-bit logical operations per clock per SM / 2 (a 64-bit
+    word takes two) x the maximum SM clock (MEASURED_PEAKS.json, else 2032 MHz)."""
+    mhz = 2032.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    except Exception:
+        pass
+    return 148 * 64 / 2 * mhz * 1e6 / 1e9
+
+
 class Clocks:
     """Samples nvidia-smi every 200 ms while the timed region runs."""
 
@@ -148,7 +161,8 @@ def main():
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--ref-budget", type=int, default=30_000_000)
     ap.add_argument("--workload", default="headline",
-                    choices=["headline", "serving", "profile-clique", "profile-iso",
+                    choices=["headline", "serving", "profile-clique", "profile-clique1m",
+                             "profile-iso",
                              "profile-hop", "profile-patterns"])
     ap.add_argument("--serving-graph", default="rmat22")
     ap.add_argument("--requests", type=int, default=1000)
@@ -204,6 +218,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     times, exps, exp_ms, exp_bytes, launches, exp_launches = [], [], [], [], 0, 0
+    tail_ms, tail_words, tail_launches = 0.0, 0, 0
     with Clocks(local) as clk:
         for _ in range(args.steps):
             r, ms = step()
@@ -213,6 +228,9 @@ def main():
             exp_bytes.append(r.stats["adj_bytes"])
             launches += r.stats["launches"]
             exp_launches += r.stats["expand_launches"]
+            tail_ms += r.stats["tail_ms"]
+            tail_words += r.stats["tail_words"]
+            tail_launches += r.stats["tail_launches"]
     torch.cuda.synchronize()
     total_ms = float(sum(times))
     total_exp = float(sum(exps))
@@ -224,13 +242,33 @@ def main():
         total_ms, total_exp = float(tm[0]), float(t[1])
     value = total_exp / (total_ms / 1e3)
     peak, peak_kind = peaks()
-    achieved = (sum(exp_bytes) / (sum(exp_ms) / 1e3)) / 1e9 if sum(exp_ms) > 0 else 0.0
-    traffic = None
+    # CSR expansion (k_clique_expand over frontier records and seeds): adjacency bytes over
+    # its own event-timed launches
+    csr_ms = max(sum(exp_ms), 1e-9)
+    achieved = (sum(exp_bytes) / (csr_ms / 1e3)) / 1e9
+    traffic = {}
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            traffic = json.load(f).get("k_clique_expand_chunglu1m")
+            traffic = json.load(f)
     except Exception:
         pass
+    roof_csr = {"bound": "hbm", "kernel": "k_clique_expand", "achieved": achieved,
+                "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
+                "traffic": traffic.get("k_clique_expand_chunglu1m"),
+                "algorithmic_bytes_per_launch": sum(exp_bytes) / max(exp_launches, 1),
+                "avg_launch_ms": csr_ms / max(exp_launches, 1), "share_of_step":
+                csr_ms / total_ms}
+    apeak = alu_peak_gops()
+    tach = (tail_words / (tail_ms / 1e3)) / 1e9 if tail_ms > 0 else 0.0
+    roof_tail = {"bound": "alu", "kernel": "k_clique_tasks<8>", "achieved": tach,
+                 "peak": apeak, "unit": "Gword-ops/s", "frac": tach / apeak,
+                 "peak_source": "derived: 148 SMs x 32 64-bit logical ops/clk x sm_max_mhz",
+                 "traffic": traffic.get("k_clique_tasks_chunglu1m"),
+                 "algorithmic_words_per_launch": tail_words / max(tail_launches, 1),
+                 "avg_launch_ms": tail_ms / max(tail_launches, 1),
+                 "share_of_step": tail_ms / total_ms}
+    dominant, secondary = ((roof_tail, roof_csr) if tail_ms > csr_ms else (roof_csr, roof_tail))
     last = r
     line = {
         "metric": METRIC, "value": value, "unit": "expansions/s", "n_gpus": world,
@@ -244,12 +282,7 @@ def main():
         "expansions_per_step": total_exp / args.steps / world,
         "threshold": last.stats["threshold"], "rounds_per_step": last.stats["rounds"],
         "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
-        "roofline": {"bound": "hbm", "kernel": "k_clique_expand", "achieved": achieved,
-                     "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
-                     "traffic": traffic,
-                     "algorithmic_bytes_per_launch": sum(exp_bytes) / max(exp_launches, 1),
-                     "avg_launch_ms": sum(exp_ms) / max(exp_launches, 1)},
+        "roofline": dominant, "roofline_secondary": secondary,
         "clocks": clk.summary(),
     }
     # end to end through the public API with host buffers: H2D of the edge list, graph build,
@@ -291,7 +324,12 @@ def _ms(r):
 def profile_case(which, nuri, sptr):
     """Small cases of each kernel family for ncu captures (a few launches, a few GB at most)."""
     import synth
-    if which == "clique":
+    if which == "clique1m":  # the headline query once (task queue size from NURI_TASK_QUEUE)
+        g = synth.workload("chunglu1m")
+        G = nuri.load_graph(g.n, g.src, g.dst, stream=sptr)
+        r = nuri.topk_cliques(G, 100, stream=sptr)
+        print(json.dumps({"case": which, "stats": r.stats}))
+    elif which == "clique":
         g = synth.chung_lu_planted(200000, 20.0, 2.1, 20, 15, 30, seed=0)
         G = nuri.load_graph(g.n, g.src, g.dst, stream=sptr)
         r = nuri.topk_cliques(G, 100, stream=sptr)

@@ -85,6 +85,10 @@ typedef struct nuri_stats {
   int64_t launches;        /* kernels of this library launched by the query       */
   int64_t expand_launches; /* launches of the expansion kernel                    */
   double expand_ms;        /* summed device time of those launches (CUDA events)  */
+  int64_t tail_launches;   /* cliques: launches of the dense-record task kernel    */
+  double tail_ms;          /* cliques: summed device time of those launches        */
+  int64_t tail_words;      /* cliques: 64-bit adjacency-row words the task kernel
+                              combined into candidate masks (colouring, branching) */
 } nuri_stats;
 
 /* A result set.  Row i has score[i]; its vertices are verts[vert_off[i] .. vert_off[i+1])

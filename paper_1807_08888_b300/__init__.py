@@ -59,6 +59,8 @@ class _Stats(ctypes.Structure):
         ("threshold", ctypes.c_int64), ("restarts", ctypes.c_int32), ("pad", ctypes.c_int32),
         ("device_ms", ctypes.c_double), ("launches", ctypes.c_int64),
         ("expand_launches", ctypes.c_int64), ("expand_ms", ctypes.c_double),
+        ("tail_launches", ctypes.c_int64), ("tail_ms", ctypes.c_double),
+        ("tail_words", ctypes.c_int64),
     ]
 
 

@@ -64,6 +64,7 @@ struct QState {
   int64_t mid_count;     // records handed to the 4-word bitmap tail
   int64_t work_next;     // dynamic work counter
   unsigned long long expansions, pruned, dequeued, adj_bytes;
+  unsigned long long tail_words;  // adjacency-row words combined by the task kernel
   int32_t hmax;          // largest clique size recorded so far
   int32_t hist[MAXD + 2];
 };
@@ -270,7 +271,8 @@ template <int W>
 __device__ void dense_node(const Ctx& cx, const WideStore& ws, int slot, int depth,
                            uint16_t* pick, unsigned long long* Pn, unsigned long long* Xn,
                            bool split, bool cont, int32_t& t_cache, unsigned long long& my_exp,
-                           unsigned long long& my_pruned, bool& limit_hit, bool& out_of_time) {
+                           unsigned long long& my_pruned, unsigned long long& my_words,
+                           bool& limit_hit, bool& out_of_time) {
   constexpr int BMW = 64 * W;
   const unsigned long long* rows = ws.rows + (int64_t)slot * BMW * W;
   const int32_t* vmap = ws.vmap + (int64_t)slot * BMW;
@@ -339,6 +341,7 @@ __device__ void dense_node(const Ctx& cx, const WideStore& ws, int slot, int dep
         while ((v = lowest<W>(cls, wa)) >= 0) {
 #pragma unroll
           for (int q = 0; q < W; ++q) cls[q] &= ~rows[v * W + q];
+          my_words += wa;
           clear_bit<W>(cls, v);
           clear_bit<W>(left, v);
           f(v, c, prefix);
@@ -358,6 +361,7 @@ __device__ void dense_node(const Ctx& cx, const WideStore& ws, int slot, int dep
       walk([&](int v, int c, const unsigned long long* prefix) {
         if (c < cmin) return;
         WTask* t = ws.q_out + base + (k++);
+        my_words += wa;
         t->slot = slot;
         t->depth = (int16_t)(depth + 1);
         for (int q = 0; q <= depth; ++q) t->picks[q] = pick[q];
@@ -437,6 +441,7 @@ __device__ void dense_node(const Ctx& cx, const WideStore& ws, int slot, int dep
           last_first = -1;
           while ((v = lowest<W>(cls, wa)) >= 0) {
             if (last_first < 0) last_first = v;
+            my_words += wa;
 #pragma unroll
             for (int q = 0; q < W; ++q) cls[q] &= ~rows[v * W + q];
             clear_bit<W>(cls, v);
@@ -465,6 +470,7 @@ __device__ void dense_node(const Ctx& cx, const WideStore& ws, int slot, int dep
       }
 #pragma unroll
       for (int q = 0; q < W; ++q) Pn[q] &= rows[branch * W + q];
+      my_words += wa;
       if (cx.maximal)
 #pragma unroll
         for (int q = 0; q < W; ++q) Xn[q] &= rows[branch * W + q];
@@ -488,7 +494,7 @@ template <int W>
 __global__ void __launch_bounds__(128) k_clique_tasks(Ctx cx, WideStore ws,
                                                       const WTask* __restrict__ in, int64_t nin,
                                                       unsigned long long* next) {
-  unsigned long long my_exp = 0, my_pruned = 0;
+  unsigned long long my_exp = 0, my_pruned = 0, my_words = 0;
   bool limit_hit = false, out_of_time = false;
   int32_t t_cache = ld_volatile(&cx.st->tau);
   while (!out_of_time) {
@@ -510,16 +516,18 @@ __global__ void __launch_bounds__(128) k_clique_tasks(Ctx cx, WideStore ws,
     }
     t_cache = ld_volatile(&cx.st->tau);
     dense_node<W>(cx, ws, T.slot, T.depth, pick, Pn, Xn, true, T.cont != 0, t_cache, my_exp,
-                  my_pruned, limit_hit, out_of_time);
+                  my_pruned, my_words, limit_hit, out_of_time);
   }
   if (limit_hit) atomicOr(&cx.st->err, 1);
   for (int o = 16; o; o >>= 1) {
     my_exp += __shfl_xor_sync(0xffffffffu, my_exp, o);
     my_pruned += __shfl_xor_sync(0xffffffffu, my_pruned, o);
+    my_words += __shfl_xor_sync(0xffffffffu, my_words, o);
   }
   if ((threadIdx.x & 31) == 0) {
     atomicAdd(&cx.st->expansions, my_exp);
     atomicAdd(&cx.st->pruned, my_pruned);
+    atomicAdd(&cx.st->tail_words, my_words);
   }
 }
 
@@ -826,8 +834,9 @@ __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
           } else {
             uint16_t pk[MAXD + 1];
             pk[0] = (uint16_t)v0;
+            unsigned long long words_here = 0;  // counted for the task kernel only
             dense_node<W>(cx, ws, slot, 0, pk, Pi, Xi, false, false, t_cache, my_exp,
-                          my_pruned, limit_hit, out_of_time);
+                          my_pruned, words_here, limit_hit, out_of_time);
           }
         }
       } else {
@@ -1332,13 +1341,37 @@ WideStore make_store(DenseBufs& B, int W, int64_t nrec, cudaStream_t s) {
   return ws;
 }
 
+// Device time and launches of the task kernel (CUDA events around every wave).
+struct TailTime {
+  double ms = 0.0;
+  int64_t launches = 0;
+  cudaEvent_t a = nullptr, b = nullptr;
+  TailTime() {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+  }
+  ~TailTime() {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+};
+
 // Dense records of one width: the warp kernel stores them and queues their children, then
-// task waves run until the queue is empty.
+// task waves run until the queue is empty.  A wave's grid is the resident capacity of the
+// task kernel (lanes take tasks dynamically).
 template <int W>
 int64_t run_dense(Ctx cx, const Rec* recs, int64_t nrec, int grid, size_t dyn, DenseBufs& B,
-                  cudaStream_t s) {
+                  TailTime& tt, cudaStream_t s) {
   int64_t launched = 0;
   const bool trace = getenv("NURI_TRACE") != nullptr;
+  static const int resident = [] {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_clique_tasks<W>, 128, 0) !=
+            cudaSuccess ||
+        per_sm < 1)
+      per_sm = 4;
+    return per_sm * sm_count();
+  }();
   WideStore ws = make_store(B, W, nrec, s);
   NURI_CUDA(cudaMemsetAsync(B.counters.p, 0, 3 * sizeof(unsigned long long), s));
   NURI_CUDA(cudaMemsetAsync(&cx.st->work_next, 0, sizeof(int64_t), s));
@@ -1347,10 +1380,18 @@ int64_t run_dense(Ctx cx, const Rec* recs, int64_t nrec, int grid, size_t dyn, D
   ++launched;
   WTask* in = B.qa.p;
   WTask* out = B.qb.p;
+  bool timed = false;  // a wave's events are pending
   while (true) {
     unsigned long long cnt = 0;
     NURI_CUDA(cudaMemcpyAsync(&cnt, B.counters.p + 1, 8, cudaMemcpyDeviceToHost, s));
     NURI_CUDA(cudaStreamSynchronize(s));
+    if (timed) {
+      float ms = 0.f;
+      NURI_CUDA(cudaEventElapsedTime(&ms, tt.a, tt.b));
+      tt.ms += ms;
+      ++tt.launches;
+      timed = false;
+    }
     int64_t n = std::min<int64_t>((int64_t)cnt, B.qcap);
     if (n == 0) break;
     int32_t err = 0;
@@ -1359,28 +1400,22 @@ int64_t run_dense(Ctx cx, const Rec* recs, int64_t nrec, int grid, size_t dyn, D
     if (err & 4) break;  // out of time: the caller reports it
     ws.q_out = out;
     NURI_CUDA(cudaMemsetAsync(B.counters.p + 1, 0, 2 * sizeof(unsigned long long), s));
-    int tgrid = (int)std::min<int64_t>((n + 127) / 128, (int64_t)sm_count() * 16);
-    cudaEvent_t a = nullptr, b = nullptr;
-    if (trace) {
-      cudaEventCreate(&a);
-      cudaEventCreate(&b);
-      cudaEventRecord(a, s);
-    }
+    int tgrid = (int)std::min<int64_t>((n + 127) / 128, (int64_t)resident);
     ws.in_next = B.counters.p + 2;
     ws.in_n = n;
+    NURI_CUDA(cudaEventRecord(tt.a, s));
     k_clique_tasks<W><<<tgrid, 128, 0, s>>>(cx, ws, in, n, B.counters.p + 2);
     NURI_CUDA(cudaGetLastError());
+    NURI_CUDA(cudaEventRecord(tt.b, s));
+    timed = true;
     if (trace) {
       float ms = 0.f;
-      cudaEventRecord(b, s);
-      cudaEventSynchronize(b);
-      cudaEventElapsedTime(&ms, a, b);
+      NURI_CUDA(cudaEventSynchronize(tt.b));
+      NURI_CUDA(cudaEventElapsedTime(&ms, tt.a, tt.b));
       unsigned long long exp = 0;
-      cudaMemcpy(&exp, &cx.st->expansions, 8, cudaMemcpyDeviceToHost);
+      NURI_CUDA(cudaMemcpy(&exp, &cx.st->expansions, 8, cudaMemcpyDeviceToHost));
       fprintf(stderr, "[nuri]   dense W=%d wave %lld: %lld tasks, %.3f ms, nodes so far %llu\n", W,
               (long long)launched, (long long)n, ms, exp);
-      cudaEventDestroy(a);
-      cudaEventDestroy(b);
     }
     ++launched;
     std::swap(in, out);
@@ -1389,10 +1424,10 @@ int64_t run_dense(Ctx cx, const Rec* recs, int64_t nrec, int grid, size_t dyn, D
 }
 
 // Narrow expansion over the batch, then the dense records it handed on (by mask width).
-// The events bracket all launches (the expansion time of the round).
+// ev0/ev1 bracket the CSR expansion launch alone; the task waves are timed in `tt`.
 int64_t launch_expand(Ctx cx, const Rec* in, const int32_t* seeds, int64_t nin, int grid,
-                      DBuf<Rec>& wide, DBuf<Rec>& mid, DenseBufs& B, cudaEvent_t ev0,
-                      cudaEvent_t ev1, cudaStream_t s) {
+                      DBuf<Rec>& wide, DBuf<Rec>& mid, DenseBufs& B, TailTime& tt,
+                      cudaEvent_t ev0, cudaEvent_t ev1, cudaStream_t s) {
   const size_t dyn1 = sizeof(unsigned long long) * KCfg<1>::WARPS * 64;
   const size_t dyn4 = sizeof(unsigned long long) * KCfg<4>::WARPS * 64 * 4 * 4;
   const size_t dynw = sizeof(unsigned long long) * KCfg<KWIDE>::WARPS * 64 * KWIDE * KWIDE;
@@ -1409,13 +1444,14 @@ int64_t launch_expand(Ctx cx, const Rec* in, const int32_t* seeds, int64_t nin, 
   memset(&none, 0, sizeof(none));
   k_clique_expand<1><<<grid, KCfg<1>::WARPS * 32, dyn1, s>>>(cx, in, seeds, nin, none);
   NURI_CUDA(cudaGetLastError());
+  NURI_CUDA(cudaEventRecord(ev1, s));
   int64_t counts[2] = {0, 0};  // wide_count, mid_count (adjacent fields)
   NURI_CUDA(cudaMemcpyAsync(counts, &cx.st->wide_count, 16, cudaMemcpyDeviceToHost, s));
   NURI_CUDA(cudaStreamSynchronize(s));
   int64_t launched = 1;
-  if (counts[1] > 0) launched += run_dense<4>(cx, mid.p, counts[1], grid, dyn4, B, s);
-  if (counts[0] > 0) launched += run_dense<KWIDE>(cx, wide.p, counts[0], grid * 2, dynw, B, s);
-  NURI_CUDA(cudaEventRecord(ev1, s));
+  if (counts[1] > 0) launched += run_dense<4>(cx, mid.p, counts[1], grid, dyn4, B, tt, s);
+  if (counts[0] > 0)
+    launched += run_dense<KWIDE>(cx, wide.p, counts[0], grid * 2, dynw, B, tt, s);
   return launched;
 }
 
@@ -1455,6 +1491,7 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
   if (g.max_out > PSMEM) pscratch.alloc((int64_t)total_warps * g.max_out, s);
   DBuf<Rec> stage, deferred, inbuf, wide, mid;
   DenseBufs dense;
+  TailTime tail;
   stage.alloc(stage_cap, s);
   ++launches;
   k_clear_stage<<<grid_for(stage_cap), 256, 0, s>>>(stage.p, stage_cap);
@@ -1519,6 +1556,8 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
   DBuf<Rec> res;
   while (true) {  // one pass; repeated only after a result-buffer overflow
     res.alloc(res_cap, s);
+    tail.ms = 0.0;
+    tail.launches = 0;
     memset(&hs, 0, sizeof(hs));
     hs.tau = tau_init;
     NURI_CUDA(cudaMemcpyAsync(st.p, &hs, sizeof(hs), cudaMemcpyHostToDevice, s));
@@ -1623,7 +1662,7 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
         if ((int64_t)wide.n < nin) wide.alloc(std::max<int64_t>(nin, 4096), s);
         if ((int64_t)mid.n < nin) mid.alloc(std::max<int64_t>(nin, 4096), s);
         cx.deferred = deferred.p;
-        launches += launch_expand(cx, inbuf.p, nullptr, nin, grid, wide, mid, dense, ev0, ev1, s);
+        launches += launch_expand(cx, inbuf.p, nullptr, nin, grid, wide, mid, dense, tail, ev0, ev1, s);
       } else {
         const int c = seed_cls;
         int64_t lo = cls_next[c];
@@ -1640,7 +1679,8 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
         if ((int64_t)wide.n < nin) wide.alloc(std::max<int64_t>(nin, 4096), s);
         if ((int64_t)mid.n < nin) mid.alloc(std::max<int64_t>(nin, 4096), s);
         cx.deferred = deferred.p;
-        launches += launch_expand(cx, nullptr, svals2.p + lo, nin, grid, wide, mid, dense, ev0, ev1, s);
+        launches += launch_expand(cx, nullptr, svals2.p + lo, nin, grid, wide, mid, dense, tail, ev0, ev1,
+                                  s);
       }
       NURI_CUDA(cudaGetLastError());
       ++rounds;
@@ -1824,6 +1864,9 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
   stats.pruned += (int64_t)hs.pruned;
   stats.dequeued += (int64_t)hs.dequeued;
   stats.adj_bytes += (int64_t)hs.adj_bytes;
+  stats.tail_words = (int64_t)hs.tail_words;
+  stats.tail_ms = tail.ms;
+  stats.tail_launches = tail.launches;
   stats.results_stored = hs.res_count;
   stats.threshold = hs.tau == INT32_MIN ? INT64_MIN : hs.tau;
   stats.restarts = restarts;
