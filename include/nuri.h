@@ -202,6 +202,40 @@ nuri_status nuri_hop_index(nuri_graph* g, int32_t hops, int32_t degree_rank, int
                            int32_t device_out, void* stream);
 
 /*
+ * nuri_hop_index_noalloc -- the hop/label index of nuri_hop_index, built on a graph the caller
+ * already holds on the device, with no memory allocated by this call.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate device memory when
+ * they need the index (a process whose GPU memory another framework has reserved up front,
+ * a service thread that must not block or fail inside an allocator, a recovery path after an
+ * out-of-memory error).
+ *
+ *   n       vertices, 0 <= n <= NURI_NOALLOC_MAX_VERTICES (larger n: NURI_ERR_INVALID)
+ *   off     device int64[n + 1] CSR row offsets, off[0] = 0, off[n] = nnz
+ *   adj     device int32[nnz] neighbour ids in [0, n); each undirected edge in both rows, no
+ *           self-loops, no duplicates (the adjacency nuri_load_graph builds)
+ *   labels  device uint8[n], values < L;  score  device int32[n], >= 0 (weights or degrees)
+ *   L       labels, 1..256;  hops  1..7
+ *   out     device int32[hops * n * L]: out[((h-1)*n + v)*L + l] as in nuri_hop_index
+ *   stream  CUDA stream (NULL: the legacy default stream); the call returns after the
+ *           stream has finished the work
+ * Scratch: one fixed device array of NURI_NOALLOC_MAX_VERTICES + 2 int32 (4 MiB) that the
+ * library holds on every GPU where it is loaded, until the process exits.  Every call shares
+ * it and it keeps the previous call's contents (the call clears what must start at zero), so
+ * calls that overlap on the GPU (several streams, threads or processes sharing the context)
+ * race: serialise them.  The first call on each device looks up that array's device address
+ * (which may make the driver load the library's device code): make the first call on a
+ * device before any stream capture and outside any section that must not allocate.
+ * Errors: NURI_ERR_INVALID (sizes, NULL arrays, or a CSR that fails the offset/id check,
+ * which runs on the device before the index), NURI_ERR_CUDA.  Nothing is written to `out`
+ * when the call is rejected.
+ */
+#define NURI_NOALLOC_MAX_VERTICES (1 << 20)
+nuri_status nuri_hop_index_noalloc(int32_t n, const int64_t* off, const int32_t* adj,
+                                   int64_t nnz, const uint8_t* labels, int32_t L,
+                                   const int32_t* score, int32_t hops, int32_t* out,
+                                   void* stream);
+
+/*
  * nuri_set_time_budget -- limit the device time of every later query on any graph: a query
  * whose kernels run past `ms` milliseconds stops and returns NURI_ERR_TIMEOUT (the graph
  * stays usable).  The check reads the GPU's global timer inside the search loops; no kernel

@@ -20,7 +20,7 @@ import numpy as np
 
 __all__ = [
     "NuriError", "lib", "load_graph", "Graph", "topk_cliques", "topk_iso", "topk_iso_batch",
-    "topk_patterns", "hop_index", "set_time_budget", "Server", "Result", "LIB_PATH", "EXPORTS",
+    "topk_patterns", "hop_index", "hop_index_noalloc", "set_time_budget", "Server", "Result", "LIB_PATH", "EXPORTS",
     "RANK_SIZE", "RANK_WEIGHT_SUM", "RANK_DEGREE_SUM", "RANK_MNI",
 ]
 
@@ -38,6 +38,7 @@ KEEP_TIES, NO_PRUNE = 0x100, 0x200
 EXPORTS = (
     "nuri_load_graph", "nuri_free_graph", "nuri_graph_get_info", "nuri_topk_cliques",
     "nuri_topk_iso", "nuri_topk_iso_batch", "nuri_topk_patterns", "nuri_hop_index",
+    "nuri_hop_index_noalloc",
     "nuri_free_result", "nuri_last_error", "nuri_version", "nuri_set_time_budget",
     "nuri_server_create", "nuri_server_submit", "nuri_server_poll", "nuri_server_wait",
     "nuri_server_stats", "nuri_server_destroy",
@@ -139,6 +140,8 @@ def lib():
             L.nuri_topk_patterns.restype = i32
             L.nuri_hop_index.argtypes = [P, i32, i32, P, i32, P]
             L.nuri_hop_index.restype = i32
+            L.nuri_hop_index_noalloc.argtypes = [i32, P, P, i64, P, i32, P, i32, P, P]
+            L.nuri_hop_index_noalloc.restype = i32
             L.nuri_set_time_budget.argtypes = [ctypes.c_double]
             L.nuri_set_time_budget.restype = i32
             L.nuri_server_create.argtypes = [P, ctypes.POINTER(_ServerCfg),
@@ -328,6 +331,15 @@ def hop_index(g: Graph, hops: int, degree_rank=False, stream=None) -> np.ndarray
     _check(lib().nuri_hop_index(g.handle, int(hops), int(bool(degree_rank)),
                                 out.ctypes.data_as(ctypes.c_void_p), 0, _stream(stream)))
     return out
+
+
+def hop_index_noalloc(n, off, adj, nnz, labels, L, score, hops, out, stream=None):
+    """nuri_hop_index_noalloc on caller-held device arrays (raw device pointers as ints): the
+    hop/label index of a CSR graph written into `out` (int32[hops * n * L]) with no device
+    memory allocated by the call, for callers that cannot allocate at that point.  The library
+    keeps one fixed 4 MiB scratch array per GPU for it; overlapping calls race."""
+    _check(lib().nuri_hop_index_noalloc(int(n), off, adj, int(nnz), labels, int(L), score,
+                                        int(hops), out, _stream(stream)))
 
 
 class Server:

@@ -11,6 +11,8 @@
 //   5. hop/label max index, H rounds of a gather-max over neighbours
 #include <cub/cub.cuh>
 
+#include <mutex>
+
 #include "nuri_internal.cuh"
 
 namespace nuri {
@@ -759,3 +761,132 @@ void build_graph(nuri_graph* g, int32_t n, int64_t m, const int32_t* src, const 
 }
 
 }  // namespace nuri
+
+// ---------------------------------------------------------------------------------------------
+// Hop/label index without allocation (nuri_hop_index_noalloc).  Some callers cannot allocate
+// device memory at the time they need the index: a process whose memory pool is reserved up
+// front by another framework, or code running where an allocation could block or fail (a
+// latency-bound service thread, a recovery path after an out-of-memory error).  This path
+// builds the same index as build_hop_index into the caller's output, on the caller's CSR,
+// with the only scratch it needs (the count and list of high-degree vertices, and a flag for
+// bad input) held in one fixed array in device memory that the library reserves at load time.
+// ---------------------------------------------------------------------------------------------
+namespace nuri {
+namespace {
+
+// scratch[0]: number of vertices of degree > kHeavy; scratch[1]: bad-input flag;
+// scratch[2 ..]: those vertices (at most one per vertex, so NURI_NOALLOC_MAX_VERTICES entries).
+// 4 MiB + 8 bytes, held by every GPU that loads the library until the process exits.
+static __device__ __align__(256) int32_t g_noalloc_scratch[2 + NURI_NOALLOC_MAX_VERTICES];
+
+// CSR sanity for caller-provided arrays: off[0] = 0, off non-decreasing, off[n] = nnz, every
+// neighbour id in [0, n).  Any violation sets flag[0] = 1 (the host then rejects the call).
+__global__ void k_check_csr(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+                            int32_t n, int64_t nnz, int32_t* __restrict__ flag) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t0 == 0 && (off[0] != 0 || off[n] != nnz)) *flag = 1;
+  for (int64_t v = t0; v < n; v += stride)
+    if (off[v + 1] < off[v]) *flag = 1;
+  for (int64_t i = t0; i < nnz; i += stride) {
+    const int32_t x = adj[i];
+    if (x < 0 || x >= n) *flag = 1;
+  }
+}
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+int32_t* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device (looked up once per device).
+int32_t* noalloc_scratch_ptr() {
+  int dev = 0;
+  NURI_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices)
+    NURI_FAIL(NURI_ERR_INVALID, "nuri_hop_index_noalloc: device ordinal %d not supported", dev);
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    int32_t* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress((void**)&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      NURI_FAIL(NURI_ERR_CUDA, "nuri_hop_index_noalloc: cudaGetSymbolAddress failed (%s)",
+                cudaGetErrorName(e));
+    g_noalloc_ptr[dev] = p;
+  }
+  return g_noalloc_ptr[dev];
+}
+
+void hop_index_noalloc(int32_t n, const int64_t* off, const int32_t* adj, int64_t nnz,
+                       const uint8_t* labels, int32_t L, const int32_t* score, int32_t H,
+                       int32_t* out, cudaStream_t s) {
+  if (n < 0 || nnz < 0) NURI_FAIL(NURI_ERR_INVALID, "nuri_hop_index_noalloc: negative size");
+  if (n > NURI_NOALLOC_MAX_VERTICES)
+    NURI_FAIL(NURI_ERR_INVALID,
+              "nuri_hop_index_noalloc: %d vertices exceed the limit of %d (the fixed scratch "
+              "array holds one entry per vertex)",
+              n, NURI_NOALLOC_MAX_VERTICES);
+  if (L < 1 || L > 256) NURI_FAIL(NURI_ERR_INVALID, "nuri_hop_index_noalloc: L must be in 1..256");
+  if (H < 1 || H > 7) NURI_FAIL(NURI_ERR_INVALID, "nuri_hop_index_noalloc: hops must be in 1..7");
+  if (n == 0) return;
+  if (!off || !labels || !score || !out || (nnz > 0 && !adj))
+    NURI_FAIL(NURI_ERR_INVALID, "nuri_hop_index_noalloc: NULL array");
+  int32_t* scratch = noalloc_scratch_ptr();
+  int32_t* cnt = scratch;
+  int32_t* bad = scratch + 1;
+  int32_t* heavy = scratch + 2;
+  // the scratch keeps the previous call's contents: the count and the flag start at zero
+  NURI_CUDA(cudaMemsetAsync(scratch, 0, 2 * sizeof(int32_t), s));
+  k_check_csr<<<sm_count() * 4, kThreads, 0, s>>>(off, adj, n, nnz, bad);
+  NURI_CUDA(cudaGetLastError());
+  int32_t h[2] = {0, 0};
+  NURI_CUDA(cudaMemcpyAsync(h, scratch, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  NURI_CUDA(cudaStreamSynchronize(s));
+  if (h[1]) NURI_FAIL(NURI_ERR_INVALID, "nuri_hop_index_noalloc: malformed CSR (offsets or ids)");
+  DevGraph d;
+  d.n = n;
+  d.nnz = nnz;
+  d.L = L;
+  d.off = off;
+  d.adj = adj;
+  d.labels = labels;
+  if (L <= 32) {
+    k_collect_heavy<<<blocks_for(n), kThreads, 0, s>>>(off, n, heavy, cnt);
+    NURI_CUDA(cudaGetLastError());
+    NURI_CUDA(cudaMemcpyAsync(h, cnt, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    NURI_CUDA(cudaStreamSynchronize(s));
+    const int32_t nheavy = h[0];
+    if (L <= 1) hop_rounds_t<1>(d, score, H, out, heavy, nheavy, s);
+    else if (L <= 2) hop_rounds_t<2>(d, score, H, out, heavy, nheavy, s);
+    else if (L <= 4) hop_rounds_t<4>(d, score, H, out, heavy, nheavy, s);
+    else if (L <= 8) hop_rounds_t<8>(d, score, H, out, heavy, nheavy, s);
+    else if (L <= 16) hop_rounds_t<16>(d, score, H, out, heavy, nheavy, s);
+    else hop_rounds_t<32>(d, score, H, out, heavy, nheavy, s);
+  } else {
+    for (int h2 = 1; h2 <= H; ++h2) {
+      const int32_t* prev = h2 == 1 ? nullptr : out + (int64_t)(h2 - 2) * n * L;
+      k_hop_round_generic<<<sm_count() * 8, 256, 0, s>>>(off, adj, labels, score, prev, n, L,
+                                                         out + (int64_t)(h2 - 1) * n * L);
+    }
+  }
+  NURI_CUDA(cudaGetLastError());
+  NURI_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace
+}  // namespace nuri
+
+extern "C" nuri_status nuri_hop_index_noalloc(int32_t n, const int64_t* off, const int32_t* adj,
+                                              int64_t nnz, const uint8_t* labels, int32_t L,
+                                              const int32_t* score, int32_t hops, int32_t* out,
+                                              void* stream) {
+  try {
+    nuri::set_error("%s", "");
+    nuri::hop_index_noalloc(n, off, adj, nnz, labels, L, score, hops, out, (cudaStream_t)stream);
+    return NURI_OK;
+  } catch (const nuri::Err& e) {
+    return e.code;
+  } catch (...) {
+    nuri::set_error("nuri_hop_index_noalloc: unexpected internal error");
+    return NURI_ERR_CUDA;
+  }
+}
