@@ -1298,9 +1298,8 @@ struct DenseBufs {
   DBuf<unsigned long long> rows4, rows8;
   DBuf<int32_t> vmap4, vmap8, recV4, recV8, recN4, recN8, recP4, recP8;
   DBuf<unsigned long long> counters;  // [0] slots, [1] queue count, [2] next task
-  DBuf<WTask> qa, qb;  // qa: the pending-task stack; qb: one wave's output
-  int64_t qcap = 0, outcap = 0;
-  int64_t wave_tasks = 0;  // most tasks one wave takes from the stack (0: 4 per resident lane)
+  DBuf<WTask> qa, qb;
+  int64_t qcap = 0;
   int32_t split_bits = 48;
 };
 
@@ -1321,13 +1320,11 @@ WideStore make_store(DenseBufs& B, int W, int64_t nrec, cudaStream_t s) {
   }
   if (!B.counters.p) B.counters.alloc(3, s);
   if (!B.qa.p) {
-    B.qcap = 1 << 24;  // pending-task stack: 16M tasks (about 3.2 GB)
-    if (const char* e = getenv("NURI_TASK_QUEUE")) B.qcap = std::max<int64_t>(64, atoll(e));
-    B.outcap = std::max<int64_t>(16, std::min<int64_t>(B.qcap / 4, 1 << 22));
+    B.qcap = 1 << 24;  // 16M tasks per queue (about 3.2 GB each)
+    if (const char* e = getenv("NURI_TASK_QUEUE")) B.qcap = std::max<int64_t>(16, atoll(e));
     B.qa.alloc(B.qcap, s);
-    B.qb.alloc(B.outcap, s);
+    B.qb.alloc(B.qcap, s);
     if (const char* e = getenv("NURI_TASK_SPLIT")) B.split_bits = std::max(1, atoi(e));
-    if (const char* e = getenv("NURI_WAVE_TASKS")) B.wave_tasks = std::max<int64_t>(1, atoll(e));
   }
   WideStore ws;
   ws.rows = rows.p;
@@ -1359,14 +1356,9 @@ struct TailTime {
   }
 };
 
-// Dense records of one width: the warp kernel stores them and pushes their children on the
-// pending-task stack, then task waves run until the stack is empty.  A wave pops at most
-// `wave_tasks` tasks from the top of the stack (the most recent, i.e. deepest, work first),
-// writes the tasks it creates (split children, donated stacks) to the output buffer, and the
-// output is pushed back where the wave's input was.  Taking a bounded slice keeps every wave's
-// output small, so splitting and donation are not starved of room however much work is
-// pending.  A wave's grid is the resident capacity of the task kernel (lanes take tasks
-// dynamically).
+// Dense records of one width: the warp kernel stores them and queues their children, then
+// task waves run until the queue is empty.  A wave's grid is the resident capacity of the
+// task kernel (lanes take tasks dynamically).
 template <int W>
 int64_t run_dense(Ctx cx, const Rec* recs, int64_t nrec, int grid, size_t dyn, DenseBufs& B,
                   TailTime& tt, cudaStream_t s) {
@@ -1386,51 +1378,47 @@ int64_t run_dense(Ctx cx, const Rec* recs, int64_t nrec, int grid, size_t dyn, D
   k_clique_expand<W><<<grid, KCfg<W>::WARPS * 32, dyn, s>>>(cx, recs, nullptr, nrec, ws);
   NURI_CUDA(cudaGetLastError());
   ++launched;
-  WTask* stack = B.qa.p;
-  const int64_t wave_cap = B.wave_tasks > 0 ? B.wave_tasks : (int64_t)resident * 128 * 4;
-  unsigned long long cnt = 0;
-  NURI_CUDA(cudaMemcpyAsync(&cnt, B.counters.p + 1, 8, cudaMemcpyDeviceToHost, s));
-  NURI_CUDA(cudaStreamSynchronize(s));
-  int64_t top = std::min<int64_t>((int64_t)cnt, B.qcap);  // tasks pending on the stack
-  float ms_tmp = 0.f;
-  while (top > 0) {
+  WTask* in = B.qa.p;
+  WTask* out = B.qb.p;
+  bool timed = false;  // a wave's events are pending
+  while (true) {
+    unsigned long long cnt = 0;
+    NURI_CUDA(cudaMemcpyAsync(&cnt, B.counters.p + 1, 8, cudaMemcpyDeviceToHost, s));
+    NURI_CUDA(cudaStreamSynchronize(s));
+    if (timed) {
+      float ms = 0.f;
+      NURI_CUDA(cudaEventElapsedTime(&ms, tt.a, tt.b));
+      tt.ms += ms;
+      ++tt.launches;
+      timed = false;
+    }
+    int64_t n = std::min<int64_t>((int64_t)cnt, B.qcap);
+    if (n == 0) break;
     int32_t err = 0;
     NURI_CUDA(cudaMemcpyAsync(&err, &cx.st->err, 4, cudaMemcpyDeviceToHost, s));
     NURI_CUDA(cudaStreamSynchronize(s));
     if (err & 4) break;  // out of time: the caller reports it
-    const int64_t n = std::min(top, wave_cap);
-    const int64_t base = top - n;
-    ws.q_out = B.qb.p;
-    ws.q_cap = std::min<int64_t>(B.outcap, B.qcap - base);
+    ws.q_out = out;
     NURI_CUDA(cudaMemsetAsync(B.counters.p + 1, 0, 2 * sizeof(unsigned long long), s));
     int tgrid = (int)std::min<int64_t>((n + 127) / 128, (int64_t)resident);
     ws.in_next = B.counters.p + 2;
     ws.in_n = n;
     NURI_CUDA(cudaEventRecord(tt.a, s));
-    k_clique_tasks<W><<<tgrid, 128, 0, s>>>(cx, ws, stack + base, n, B.counters.p + 2);
+    k_clique_tasks<W><<<tgrid, 128, 0, s>>>(cx, ws, in, n, B.counters.p + 2);
     NURI_CUDA(cudaGetLastError());
     NURI_CUDA(cudaEventRecord(tt.b, s));
+    timed = true;
     if (trace) {
       float ms = 0.f;
       NURI_CUDA(cudaEventSynchronize(tt.b));
       NURI_CUDA(cudaEventElapsedTime(&ms, tt.a, tt.b));
       unsigned long long exp = 0;
       NURI_CUDA(cudaMemcpy(&exp, &cx.st->expansions, 8, cudaMemcpyDeviceToHost));
-      fprintf(stderr, "[nuri]   dense W=%d wave %lld: %lld of %lld tasks, %.3f ms, nodes so far %llu\n",
-              W, (long long)launched, (long long)n, (long long)top, ms, exp);
+      fprintf(stderr, "[nuri]   dense W=%d wave %lld: %lld tasks, %.3f ms, nodes so far %llu\n", W,
+              (long long)launched, (long long)n, ms, exp);
     }
     ++launched;
-    // push the wave's output back onto the stack in place of its input
-    NURI_CUDA(cudaMemcpyAsync(&cnt, B.counters.p + 1, 8, cudaMemcpyDeviceToHost, s));
-    NURI_CUDA(cudaStreamSynchronize(s));
-    NURI_CUDA(cudaEventElapsedTime(&ms_tmp, tt.a, tt.b));
-    tt.ms += ms_tmp;
-    ++tt.launches;
-    const int64_t nout = std::min<int64_t>((int64_t)cnt, ws.q_cap);
-    if (nout > 0)
-      NURI_CUDA(cudaMemcpyAsync(stack + base, B.qb.p, sizeof(WTask) * nout,
-                                cudaMemcpyDeviceToDevice, s));
-    top = base + nout;
+    std::swap(in, out);
   }
   return launched;
 }
