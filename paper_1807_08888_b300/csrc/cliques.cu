@@ -192,6 +192,14 @@ __device__ __forceinline__ int lowest(const unsigned long long* X, int wa) {
 }
 
 template <int W>
+__device__ __forceinline__ int highest(const unsigned long long* X, int wa) {
+#pragma unroll
+  for (int q = W - 1; q >= 0; --q)
+    if (q < wa && X[q]) return q * 64 + 63 - __clzll((long long)X[q]);
+  return -1;
+}
+
+template <int W>
 __device__ __forceinline__ int popc(const unsigned long long* X, int wa) {
   int c = 0;
 #pragma unroll
@@ -383,109 +391,133 @@ __device__ void dense_node(const Ctx& cx, const WideStore& ws, int slot, int dep
     for (unsigned long long q = base; q < base + r && (int64_t)q < ws.q_cap; ++q)
       ws.q_out[q].slot = -1;
   }
-  // ---- finish the subtree here: colour-ordered branching with a per-level stack ----
+  // ---- finish the subtree here: colour once per node, branch over its high-colour set ----
+  // Level l keeps rem (candidates not yet branched on), R (high-colour candidates not yet
+  // branched on) and, in maximal mode, X (explored).  A node's R is what is left of its
+  // candidates after greedy colour classes 1 .. tau - |node| - 1 (those that cannot lift a
+  // clique to tau) are taken out; its children come from R, highest index first, child u
+  // having the candidates (rem - u) & N(u), so each clique below the node is reached once,
+  // through the first of its vertices to be branched on.  The colouring is done once per node.
   unsigned long long stkP[MAXD][W];
+  unsigned long long stkR[MAXD][W];
   unsigned long long stkX[MAXD][W];
   const int base_depth = depth;
-  int local = 0;  // nodes visited by this call
+  int local = 0;      // nodes entered by this call
+  bool fresh = true;  // the node at `depth` (candidates Pn) has not been coloured yet
   while (!out_of_time) {
-    int size = nv + depth + 1;
-    // hand the rest of the stack on once the wave's input is used up (and the queue has room)
-    if (split && ++local >= 16 && (local & 15) == 0 && depth < TPICKS &&
-        (int64_t)ld_volatile(ws.in_next) >= ws.in_n &&
-        (int64_t)ld_volatile(ws.q_count) < ws.q_cap / 2) {
-      int r = any<W>(Pn, wa) ? 1 : 0;
-      for (int l = base_depth; l < depth; ++l) r += any<W>(stkP[l], wa) ? 1 : 0;
-      const unsigned long long base = r ? atomicAdd(ws.q_count, (unsigned long long)r) : 0ull;
-      if (r == 0) break;
-      if ((int64_t)(base + r) <= ws.q_cap) {
-        int k = 0;
-        for (int l = base_depth; l <= depth; ++l) {
-          const unsigned long long* PL = l < depth ? stkP[l] : Pn;
-          const unsigned long long* XL = l < depth ? stkX[l] : Xn;
-          if (!any<W>(PL, wa)) continue;
-          WTask* t = ws.q_out + base + (k++);
-          t->slot = slot;
-          t->depth = (int16_t)l;
-          t->cont = 1;
-          for (int q = 0; q <= l; ++q) t->picks[q] = pick[q];
+    bool level_ok = true;
+    if (fresh) {
+      fresh = false;
+      const int size = nv + depth + 1;
+      // hand the rest of the stack on once the wave's input is used up (and there is room):
+      // the current node and every level below it that still has vertices to branch on
+      if (split && ++local >= 16 && (local & 15) == 0 && depth < TPICKS &&
+          (int64_t)ld_volatile(ws.in_next) >= ws.in_n &&
+          (int64_t)ld_volatile(ws.q_count) < ws.q_cap / 2) {
+        int r = any<W>(Pn, wa) ? 1 : 0;
+        for (int l = base_depth; l < depth; ++l) r += any<W>(stkR[l], wa) ? 1 : 0;
+        if (r == 0) break;
+        const unsigned long long base = atomicAdd(ws.q_count, (unsigned long long)r);
+        if ((int64_t)(base + r) <= ws.q_cap) {
+          int k = 0;
+          for (int l = base_depth; l <= depth; ++l) {
+            if (l < depth ? !any<W>(stkR[l], wa) : !any<W>(Pn, wa)) continue;
+            const unsigned long long* PL = l < depth ? stkP[l] : Pn;
+            const unsigned long long* XL = l < depth ? stkX[l] : Xn;
+            WTask* t = ws.q_out + base + (k++);
+            t->slot = slot;
+            t->depth = (int16_t)l;
+            t->cont = 1;
+            for (int q = 0; q <= l; ++q) t->picks[q] = pick[q];
 #pragma unroll
-          for (int q = 0; q < KWIDE; ++q) {
-            t->P[q] = q < W ? PL[q] : 0ull;
-            if (cx.maximal) t->X[q] = q < W ? XL[q] : 0ull;
+            for (int q = 0; q < KWIDE; ++q) {
+              t->P[q] = q < W ? PL[q] : 0ull;
+              if (cx.maximal) t->X[q] = q < W ? XL[q] : 0ull;
+            }
           }
+          return;
         }
-        return;
+        for (unsigned long long q = base; q < base + r && (int64_t)q < ws.q_cap; ++q)
+          ws.q_out[q].slot = -1;
+        local = INT32_MIN;  // no room: finish here
       }
-      for (unsigned long long q = base; q < base + r && (int64_t)q < ws.q_cap; ++q)
-        ws.q_out[q].slot = -1;
-      local = INT32_MIN;  // no room: finish here
-    }
-    int branch = -1;
-    if (any<W>(Pn, wa)) {
-      if (size >= MAXD) {
-        limit_hit = true;
-      } else if (cx.no_prune) {
-        branch = lowest<W>(Pn, wa);
-      } else {
-        unsigned long long left[W];
+      unsigned long long R[W];
 #pragma unroll
-        for (int q = 0; q < W; ++q) left[q] = Pn[q];
-        int colours = 0, last_first = -1;
-        while (any<W>(left, wa) && size + colours < t_cache) {
-          ++colours;
+      for (int q = 0; q < W; ++q) R[q] = Pn[q];
+      level_ok = any<W>(R, wa);
+      if (level_ok && size >= MAXD) {
+        limit_hit = true;
+        level_ok = false;
+      }
+      if (level_ok && !cx.no_prune && size < t_cache) {
+        const int kmin = t_cache - size;  // classes 1 .. kmin-1 cannot reach tau
+        for (int c = 1; c < kmin && any<W>(R, wa); ++c) {
           unsigned long long cls[W];
 #pragma unroll
-          for (int q = 0; q < W; ++q) cls[q] = left[q];
+          for (int q = 0; q < W; ++q) cls[q] = R[q];
           int v;
-          last_first = -1;
           while ((v = lowest<W>(cls, wa)) >= 0) {
-            if (last_first < 0) last_first = v;
             my_words += wa;
 #pragma unroll
             for (int q = 0; q < W; ++q) cls[q] &= ~rows[v * W + q];
             clear_bit<W>(cls, v);
-            clear_bit<W>(left, v);
+            clear_bit<W>(R, v);
           }
         }
-        if (any<W>(left, wa)) branch = lowest<W>(left, wa);  // a high-colour vertex
-        else if (size + colours >= t_cache) branch = last_first;
-        else ++my_pruned;
+        if (!any<W>(R, wa)) {
+          ++my_pruned;
+          level_ok = false;
+        }
+      }
+      if (level_ok) {
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+          stkP[depth][q] = Pn[q];
+          stkR[depth][q] = R[q];
+        }
+        if (cx.maximal)
+#pragma unroll
+          for (int q = 0; q < W; ++q) stkX[depth][q] = Xn[q];
       }
     }
-    if (branch >= 0) {
-      unsigned long long sp2[W], sx2[W];
+    if (level_ok) {
+      unsigned long long R[W];
 #pragma unroll
-      for (int q = 0; q < W; ++q) {
-        sp2[q] = Pn[q];
-        sx2[q] = Xn[q];
+      for (int q = 0; q < W; ++q) R[q] = stkR[depth][q];
+      const int u = highest<W>(R, wa);
+      if (u >= 0) {
+        unsigned long long rem[W];
+#pragma unroll
+        for (int q = 0; q < W; ++q) rem[q] = stkP[depth][q];
+        clear_bit<W>(R, u);
+        clear_bit<W>(rem, u);
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+          stkR[depth][q] = R[q];
+          stkP[depth][q] = rem[q];
+          Pn[q] = rem[q] & rows[u * W + q];
+        }
+        my_words += wa;
+        if (cx.maximal) {
+          unsigned long long xs[W];
+#pragma unroll
+          for (int q = 0; q < W; ++q) {
+            xs[q] = stkX[depth][q];
+            Xn[q] = xs[q] & rows[u * W + q];
+          }
+          set_bit<W>(xs, u);
+#pragma unroll
+          for (int q = 0; q < W; ++q) stkX[depth][q] = xs[q];
+        }
+        ++depth;
+        pick[depth] = (uint16_t)u;
+        visit_node(depth, Pn, Xn);
+        fresh = true;
+        continue;
       }
-      clear_bit<W>(sp2, branch);
-#pragma unroll
-      for (int q = 0; q < W; ++q) stkP[depth][q] = sp2[q];
-      if (cx.maximal) {
-        set_bit<W>(sx2, branch);
-#pragma unroll
-        for (int q = 0; q < W; ++q) stkX[depth][q] = sx2[q];
-      }
-#pragma unroll
-      for (int q = 0; q < W; ++q) Pn[q] &= rows[branch * W + q];
-      my_words += wa;
-      if (cx.maximal)
-#pragma unroll
-        for (int q = 0; q < W; ++q) Xn[q] &= rows[branch * W + q];
-      ++depth;
-      pick[depth] = (uint16_t)branch;
-      visit_node(depth, Pn, Xn);
-      continue;
     }
     if (depth == base_depth) break;
     --depth;
-#pragma unroll
-    for (int q = 0; q < W; ++q) Pn[q] = stkP[depth][q];
-    if (cx.maximal)
-#pragma unroll
-      for (int q = 0; q < W; ++q) Xn[q] = stkX[depth][q];
   }
 }
 
@@ -944,6 +976,7 @@ __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
       // per-lane DFS stack: the untried candidates (and, for maximality, the explored ones)
       // of every level; pick[d] = index in P of the vertex added at depth d
       unsigned long long stkP[MAXD][W];
+      unsigned long long stkR[MAXD][W];
       unsigned long long stkX[MAXD][W];
       uint16_t pick[MAXD + 1];
       // ---- phase 2: grandchild subtrees, taken dynamically ----
@@ -994,10 +1027,13 @@ __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
         int depth = 1;
         pick[0] = (uint16_t)ord[i];
         pick[1] = (uint16_t)j;
-        // visit the node (record + picks[0..depth], candidates Pn, explored Xn), then branch
+        // visit the node (record + picks[0..depth], candidates Pn, explored Xn), colour it once,
+        // then branch over its high-colour set (as in dense_node: level d keeps the untried
+        // candidates stkP, the untried high-colour ones stkR and the explored ones stkX)
         bool visit = true;
         while (true) {
           int size = nv + depth + 1;
+          bool level_ok = true;
           if (visit) {
             ++my_exp;
             if ((my_exp & 31) == 0) {
@@ -1027,75 +1063,83 @@ __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
               }
             }
             visit = false;
-          }
-          // branch: colour the untried candidates; stop when they cannot reach tau
-          int branch = -1;
-          if (any<W>(Pn, wa)) {
-            if (size >= MAXD) {
-              limit_hit = true;
-            } else if (cx.no_prune) {
-              branch = lowest<W>(Pn, wa);
-            } else {
-              unsigned long long left[W];
+            // colour once: R = the candidates left after classes 1 .. tau-|node|-1
+            unsigned long long R[W];
 #pragma unroll
-              for (int q = 0; q < W; ++q) left[q] = Pn[q];
-              int colours = 0, last_first = -1;
-              while (any<W>(left, wa) && size + colours < t_cache) {
-                ++colours;
+            for (int q = 0; q < W; ++q) R[q] = Pn[q];
+            level_ok = any<W>(R, wa);
+            if (level_ok && size >= MAXD) {
+              limit_hit = true;
+              level_ok = false;
+            }
+            if (level_ok && !cx.no_prune && size < t_cache) {
+              const int kmin = t_cache - size;
+              for (int c = 1; c < kmin && any<W>(R, wa); ++c) {
                 unsigned long long cls[W];
 #pragma unroll
-                for (int q = 0; q < W; ++q) cls[q] = left[q];
+                for (int q = 0; q < W; ++q) cls[q] = R[q];
                 int v;
-                last_first = -1;
                 while ((v = lowest<W>(cls, wa)) >= 0) {
-                  if (last_first < 0) last_first = v;
 #pragma unroll
                   for (int q = 0; q < W; ++q) cls[q] &= ~rows[v * W + q];
                   clear_bit<W>(cls, v);
-                  clear_bit<W>(left, v);
+                  clear_bit<W>(R, v);
                 }
               }
-              if (any<W>(left, wa)) branch = lowest<W>(left, wa);  // a high-colour vertex
-              else if (size + colours >= t_cache) branch = last_first;
-              else ++my_pruned;
+              if (!any<W>(R, wa)) {
+                ++my_pruned;
+                level_ok = false;
+              }
             }
-          }
-          if (branch >= 0) {
-            // child: add `branch`; it leaves the untried candidates of this node
-            {
-              unsigned long long sp2[W], sx2[W];
+            if (level_ok) {
 #pragma unroll
               for (int q = 0; q < W; ++q) {
-                sp2[q] = Pn[q];
-                sx2[q] = Xn[q];
+                stkP[depth][q] = Pn[q];
+                stkR[depth][q] = R[q];
               }
-              clear_bit<W>(sp2, branch);
+              if (cx.maximal)
 #pragma unroll
-              for (int q = 0; q < W; ++q) stkP[depth][q] = sp2[q];
-              if (cx.maximal) {  // the explored set only matters for maximality
-                set_bit<W>(sx2, branch);
-#pragma unroll
-                for (int q = 0; q < W; ++q) stkX[depth][q] = sx2[q];
-              }
+                for (int q = 0; q < W; ++q) stkX[depth][q] = Xn[q];
             }
-#pragma unroll
-            for (int q = 0; q < W; ++q) Pn[q] &= rows[branch * W + q];
-            if (cx.maximal)
-#pragma unroll
-              for (int q = 0; q < W; ++q) Xn[q] &= rows[branch * W + q];
-            ++depth;
-            pick[depth] = (uint16_t)branch;
-            visit = true;
-            continue;
           }
-          // done with this node: back to its parent's remaining candidates
+          if (level_ok) {
+            unsigned long long R[W];
+#pragma unroll
+            for (int q = 0; q < W; ++q) R[q] = stkR[depth][q];
+            const int u = highest<W>(R, wa);
+            if (u >= 0) {
+              // child: add u; its candidates are this node's untried ones adjacent to u
+              unsigned long long rem[W];
+#pragma unroll
+              for (int q = 0; q < W; ++q) rem[q] = stkP[depth][q];
+              clear_bit<W>(R, u);
+              clear_bit<W>(rem, u);
+#pragma unroll
+              for (int q = 0; q < W; ++q) {
+                stkR[depth][q] = R[q];
+                stkP[depth][q] = rem[q];
+                Pn[q] = rem[q] & rows[u * W + q];
+              }
+              if (cx.maximal) {  // the explored set only matters for maximality
+                unsigned long long xs[W];
+#pragma unroll
+                for (int q = 0; q < W; ++q) {
+                  xs[q] = stkX[depth][q];
+                  Xn[q] = xs[q] & rows[u * W + q];
+                }
+                set_bit<W>(xs, u);
+#pragma unroll
+                for (int q = 0; q < W; ++q) stkX[depth][q] = xs[q];
+              }
+              ++depth;
+              pick[depth] = (uint16_t)u;
+              visit = true;
+              continue;
+            }
+          }
+          // done with this node: back to its parent
           if (depth == 1) break;
           --depth;
-#pragma unroll
-          for (int q = 0; q < W; ++q) Pn[q] = stkP[depth][q];
-          if (cx.maximal)
-#pragma unroll
-            for (int q = 0; q < W; ++q) Xn[q] = stkX[depth][q];
         }
       }
       }
