@@ -1385,6 +1385,74 @@ WideStore make_store(DenseBufs& B, int W, int64_t nrec, cudaStream_t s) {
   return ws;
 }
 
+// Candidate results of size >= tau, copied from `in` to `out` (order not kept: the top-k merge
+// sorts).  Rows below tau can never enter the top k, since tau only rises.
+__global__ void k_compact_results(const Rec* __restrict__ in, int64_t n, int32_t tau,
+                                  Rec* __restrict__ out, unsigned long long* __restrict__ cnt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < n; i += nwarps) {  // one warp per row
+    const int nv = in[i].nv;
+    if (nv < tau) continue;
+    unsigned long long slot = 0;
+    if (lane == 0) slot = atomicAdd(cnt, 1ull);
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    Rec* o = out + slot;
+    if (lane == 0) {
+      o->nv = nv;
+      o->bound = in[i].bound;
+    }
+    for (int a = lane; a < nv; a += 32) o->V[a] = in[i].V[a];
+  }
+}
+
+// The device result set of one query pass.
+struct ResultStore {
+  DBuf<Rec> buf;
+  int64_t cap = 0;
+  DBuf<unsigned long long> cnt;
+};
+
+// Once the result set is half full, keep only its rows of size >= tau (into a buffer four
+// times the rows kept, at least the current capacity), so that a long query does not
+// overflow the set with cliques that tau has since passed.  A set that has already
+// overflowed (rows lost) is left alone: the pass is then re-run with the final tau.
+void compact_results(Ctx& cx, ResultStore& rs, cudaStream_t s) {
+  int64_t rc = 0;
+  int32_t tau = 0;
+  NURI_CUDA(cudaMemcpyAsync(&rc, &cx.st->res_count, 8, cudaMemcpyDeviceToHost, s));
+  NURI_CUDA(cudaMemcpyAsync(&tau, &cx.st->tau, 4, cudaMemcpyDeviceToHost, s));
+  NURI_CUDA(cudaStreamSynchronize(s));
+  if (rc <= rs.cap / 2 || rc > rs.cap) return;
+  if (!rs.cnt.p) rs.cnt.alloc(1, s);
+  NURI_CUDA(cudaMemsetAsync(rs.cnt.p, 0, 8, s));
+  DBuf<Rec> nb;
+  nb.alloc(rs.cap, s);
+  k_compact_results<<<std::max(1, std::min<int>((int)((rc + 7) / 8), sm_count() * 16)), 256, 0, s>>>(
+      rs.buf.p, rc, tau, nb.p, rs.cnt.p);
+  NURI_CUDA(cudaGetLastError());
+  unsigned long long kept = 0;
+  NURI_CUDA(cudaMemcpyAsync(&kept, rs.cnt.p, 8, cudaMemcpyDeviceToHost, s));
+  NURI_CUDA(cudaStreamSynchronize(s));
+  int64_t cap = rs.cap;
+  if ((int64_t)kept * 4 > cap) {
+    cap = (int64_t)kept * 4;
+    DBuf<Rec> big;
+    big.alloc(cap, s);
+    if (kept)
+      NURI_CUDA(cudaMemcpyAsync(big.p, nb.p, sizeof(Rec) * kept, cudaMemcpyDeviceToDevice, s));
+    nb = std::move(big);
+  }
+  rs.buf = std::move(nb);
+  rs.cap = cap;
+  const int64_t kept64 = (int64_t)kept;
+  NURI_CUDA(cudaMemcpyAsync(&cx.st->res_count, &kept64, 8, cudaMemcpyHostToDevice, s));
+  NURI_CUDA(cudaStreamSynchronize(s));
+  cx.res = rs.buf.p;
+  cx.res_cap = rs.cap;
+}
+
 // Device time and launches of the task kernel (CUDA events around every wave).
 struct TailTime {
   double ms = 0.0;
@@ -1405,7 +1473,7 @@ struct TailTime {
 // task kernel (lanes take tasks dynamically).
 template <int W>
 int64_t run_dense(Ctx cx, const Rec* recs, int64_t nrec, int grid, size_t dyn, DenseBufs& B,
-                  TailTime& tt, cudaStream_t s) {
+                  TailTime& tt, ResultStore& rs, cudaStream_t s) {
   int64_t launched = 0;
   const bool trace = getenv("NURI_TRACE") != nullptr;
   static const int resident = [] {
@@ -1438,6 +1506,7 @@ int64_t run_dense(Ctx cx, const Rec* recs, int64_t nrec, int grid, size_t dyn, D
     }
     int64_t n = std::min<int64_t>((int64_t)cnt, B.qcap);
     if (n == 0) break;
+    compact_results(cx, rs, s);
     int32_t err = 0;
     NURI_CUDA(cudaMemcpyAsync(&err, &cx.st->err, 4, cudaMemcpyDeviceToHost, s));
     NURI_CUDA(cudaStreamSynchronize(s));
@@ -1471,7 +1540,7 @@ int64_t run_dense(Ctx cx, const Rec* recs, int64_t nrec, int grid, size_t dyn, D
 // ev0/ev1 bracket the CSR expansion launch alone; the task waves are timed in `tt`.
 int64_t launch_expand(Ctx cx, const Rec* in, const int32_t* seeds, int64_t nin, int grid,
                       DBuf<Rec>& wide, DBuf<Rec>& mid, DenseBufs& B, TailTime& tt,
-                      cudaEvent_t ev0, cudaEvent_t ev1, cudaStream_t s) {
+                      ResultStore& rs, cudaEvent_t ev0, cudaEvent_t ev1, cudaStream_t s) {
   const size_t dyn1 = sizeof(unsigned long long) * KCfg<1>::WARPS * 64;
   const size_t dyn4 = sizeof(unsigned long long) * KCfg<4>::WARPS * 64 * 4 * 4;
   const size_t dynw = sizeof(unsigned long long) * KCfg<KWIDE>::WARPS * 64 * KWIDE * KWIDE;
@@ -1493,9 +1562,14 @@ int64_t launch_expand(Ctx cx, const Rec* in, const int32_t* seeds, int64_t nin, 
   NURI_CUDA(cudaMemcpyAsync(counts, &cx.st->wide_count, 16, cudaMemcpyDeviceToHost, s));
   NURI_CUDA(cudaStreamSynchronize(s));
   int64_t launched = 1;
-  if (counts[1] > 0) launched += run_dense<4>(cx, mid.p, counts[1], grid, dyn4, B, tt, s);
-  if (counts[0] > 0)
-    launched += run_dense<KWIDE>(cx, wide.p, counts[0], grid * 2, dynw, B, tt, s);
+  if (counts[1] > 0) {
+    compact_results(cx, rs, s);
+    launched += run_dense<4>(cx, mid.p, counts[1], grid, dyn4, B, tt, rs, s);
+  }
+  if (counts[0] > 0) {
+    compact_results(cx, rs, s);
+    launched += run_dense<KWIDE>(cx, wide.p, counts[0], grid * 2, dynw, B, tt, rs, s);
+  }
   return launched;
 }
 
@@ -1597,9 +1671,10 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
     }
   } evg{ev0, ev1};
 
-  DBuf<Rec> res;
+  ResultStore rs;
   while (true) {  // one pass; repeated only after a result-buffer overflow
-    res.alloc(res_cap, s);
+    rs.buf.alloc(res_cap, s);
+    rs.cap = res_cap;
     tail.ms = 0.0;
     tail.launches = 0;
     memset(&hs, 0, sizeof(hs));
@@ -1623,8 +1698,8 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
     Ctx cx;
     cx.g = g;
     cx.st = st.p;
-    cx.res = res.p;
-    cx.res_cap = res_cap;
+    cx.res = rs.buf.p;
+    cx.res_cap = rs.cap;
     cx.stage = stage.p;
     cx.stage_cap = stage_cap;
     cx.pscratch = pscratch.p;
@@ -1649,6 +1724,7 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
                   "nuri_topk_cliques: time budget exhausted after %lld rounds (%llu nodes "
                   "visited, tau %d)",
                   (long long)rounds, (unsigned long long)hs.expansions, hs.tau);
+      compact_results(cx, rs, s);
       int32_t tau = hs.tau;
       // highest bucket with pending seeds (narrow class first) or frontier records
       int b_seed = -1, b_front = -1, seed_cls = -1;
@@ -1706,7 +1782,10 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
         if ((int64_t)wide.n < nin) wide.alloc(std::max<int64_t>(nin, 4096), s);
         if ((int64_t)mid.n < nin) mid.alloc(std::max<int64_t>(nin, 4096), s);
         cx.deferred = deferred.p;
-        launches += launch_expand(cx, inbuf.p, nullptr, nin, grid, wide, mid, dense, tail, ev0, ev1, s);
+        launches += launch_expand(cx, inbuf.p, nullptr, nin, grid, wide, mid, dense, tail, rs, ev0,
+                                  ev1, s);
+        cx.res = rs.buf.p;
+        cx.res_cap = rs.cap;
       } else {
         const int c = seed_cls;
         int64_t lo = cls_next[c];
@@ -1723,8 +1802,10 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
         if ((int64_t)wide.n < nin) wide.alloc(std::max<int64_t>(nin, 4096), s);
         if ((int64_t)mid.n < nin) mid.alloc(std::max<int64_t>(nin, 4096), s);
         cx.deferred = deferred.p;
-        launches += launch_expand(cx, nullptr, svals2.p + lo, nin, grid, wide, mid, dense, tail, ev0, ev1,
-                                  s);
+        launches += launch_expand(cx, nullptr, svals2.p + lo, nin, grid, wide, mid, dense, tail, rs,
+                                  ev0, ev1, s);
+        cx.res = rs.buf.p;
+        cx.res_cap = rs.cap;
       }
       NURI_CUDA(cudaGetLastError());
       ++rounds;
@@ -1818,11 +1899,11 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
       b.count = 0;
     }
     stats.rounds += rounds;
-    if (hs.res_count > res_cap) {
+    if (hs.res_count > rs.cap) {
       // every result with size >= tau_final was counted: re-run with that threshold and room
       int64_t need = 0;
       for (int c = std::max(hs.tau, 0); c <= MAXD; ++c) need += hs.hist[c];
-      res_cap = std::max<int64_t>(need + 1024, res_cap);
+      res_cap = std::max<int64_t>(need + 1024, rs.cap);
       tau_init = hs.tau;
       ++restarts;
       continue;
@@ -1839,7 +1920,7 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
   nsel.alloc(1, s);
   flag.alloc(1, s);
   NURI_CUDA(cudaMemsetAsync(nsel.p, 0, 4, s));
-  if (cnt > 0) { ++launches; k_select<<<grid_for(cnt), 256, 0, s>>>(res.p, cnt, tau, g, flag.p, selV.p, selN.p, nsel.p); }
+  if (cnt > 0) { ++launches; k_select<<<grid_for(cnt), 256, 0, s>>>(rs.buf.p, cnt, tau, g, flag.p, selV.p, selN.p, nsel.p); }
   int32_t ns = 0;
   NURI_CUDA(cudaMemcpyAsync(&ns, nsel.p, 4, cudaMemcpyDeviceToHost, s));
   NURI_CUDA(cudaStreamSynchronize(s));

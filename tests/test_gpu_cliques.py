@@ -179,6 +179,18 @@ def test_result_overflow_restart_is_exact(monkeypatch):
     assert [(r[0], r[1]) for r in got] == want
 
 
+def test_result_compaction_keeps_the_top_k(monkeypatch):
+    # a small result set fills up across rounds: rows below tau are dropped on the way and the
+    # answer is unchanged (compaction, not a re-run, when no single launch overflows it)
+    g = synth.chung_lu_planted(20000, 20.0, 2.1, 10, 8, 16, seed=7)
+    G = load(g)
+    ref = nuri.topk_cliques(G, 50)
+    monkeypatch.setenv("NURI_RESULT_CAP", "512")
+    got = nuri.topk_cliques(G, 50)
+    monkeypatch.delenv("NURI_RESULT_CAP")
+    assert [(r[0], r[1]) for r in got] == [(r[0], r[1]) for r in ref]
+
+
 def test_edge_cases():
     # empty graph, isolated vertices, self-loops and duplicate pairs
     G = nuri.load_graph(0, np.zeros(0, np.int32), np.zeros(0, np.int32))
