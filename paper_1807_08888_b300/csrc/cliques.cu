@@ -160,6 +160,17 @@ __device__ void add_result(const Ctx& cx, const int32_t* V, int nv, int32_t extr
   }
   atomicAdd(&cx.st->hist[c], 1);
   if (c > ld_volatile(&cx.st->hmax)) atomicMax(&cx.st->hmax, c);
+  if (!cx.maximal && c > ld_volatile(&cx.st->tau)) {
+    // every subset of a clique is a clique: one of size c holds C(c, s) cliques of size s, so
+    // the k-th best size is at least the largest s with C(c, s) >= k
+    double b = 1.0;  // C(c, s)
+    int s = c;
+    while (s > 1 && b < (double)cx.k) {
+      b = b * s / (double)(c - s + 1);
+      --s;
+    }
+    if (b >= (double)cx.k && s > ld_volatile(&cx.st->tau)) atomicMax(&cx.st->tau, s);
+  }
   if ((int64_t)(slot + 1) < (int64_t)cx.k) return;  // fewer than k results so far
   publish_threshold(cx.st->hist, ld_volatile(&cx.st->hmax), 0, cx.k, &cx.st->tau);
 }
