@@ -1537,9 +1537,13 @@ int64_t run_dense(Ctx cx, const Rec* recs, int64_t nrec, int grid, size_t dyn, D
       NURI_CUDA(cudaEventSynchronize(tt.b));
       NURI_CUDA(cudaEventElapsedTime(&ms, tt.a, tt.b));
       unsigned long long exp = 0;
+      int64_t nres = 0;
       NURI_CUDA(cudaMemcpy(&exp, &cx.st->expansions, 8, cudaMemcpyDeviceToHost));
-      fprintf(stderr, "[nuri]   dense W=%d wave %lld: %lld tasks, %.3f ms, nodes so far %llu\n", W,
-              (long long)launched, (long long)n, ms, exp);
+      NURI_CUDA(cudaMemcpy(&nres, &cx.st->res_count, 8, cudaMemcpyDeviceToHost));
+      fprintf(stderr,
+              "[nuri]   dense W=%d wave %lld: %lld tasks, %.3f ms, nodes so far %llu, results "
+              "%lld of %lld\n",
+              W, (long long)launched, (long long)n, ms, exp, (long long)nres, (long long)rs.cap);
     }
     ++launched;
     std::swap(in, out);
@@ -1724,7 +1728,9 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
     // smaller split limit (exercises the frontier tier in tests)
     if (const char* e = getenv("NURI_SPLIT_ABOVE")) cx.split_above = std::max(1, atoi(e));
     int64_t rounds = 0;
-    int64_t seed_chunk = std::max<int64_t>(total_warps, 1024);
+    // the first chunk is small: with tau still unset every node is a result, so a wide first
+    // launch would fill the result set with small cliques; the chunk doubles every seed round
+    int64_t seed_chunk = 512;
 
     while (true) {
       NURI_CUDA(cudaMemcpyAsync(&hs, st.p, sizeof(hs), cudaMemcpyDeviceToHost, s));
@@ -1824,11 +1830,17 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
         float ms = 0.f;
         NURI_CUDA(cudaStreamSynchronize(s));
         NURI_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
-        int64_t nwide = 0;
+        int64_t nwide = 0, nres = 0;
+        int32_t tau_now = 0;
         NURI_CUDA(cudaMemcpy(&nwide, &st.p->wide_count, 8, cudaMemcpyDeviceToHost));
-        fprintf(stderr, "[nuri] round %lld %s bucket %d n %lld wide %lld tau %d: %.3f ms\n",
+        NURI_CUDA(cudaMemcpy(&nres, &st.p->res_count, 8, cudaMemcpyDeviceToHost));
+        NURI_CUDA(cudaMemcpy(&tau_now, &st.p->tau, 4, cudaMemcpyDeviceToHost));
+        fprintf(stderr,
+                "[nuri] round %lld %s bucket %d n %lld wide %lld tau %d -> %d, results %lld of "
+                "%lld: %.3f ms\n",
                 (long long)rounds, src_bucket >= 0 ? "frontier" : (narrow_first ? "narrow" : "seeds"),
-                b_front >= b_seed ? b_front : b_seed, (long long)nin, (long long)nwide, tau, ms);
+                b_front >= b_seed ? b_front : b_seed, (long long)nin, (long long)nwide, tau,
+                tau_now, (long long)nres, (long long)rs.cap, ms);
       }
       // staging (children) and deferred parents -> buckets, by bound
       int64_t scnt = 0, dcnt = 0;
