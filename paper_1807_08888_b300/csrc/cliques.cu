@@ -244,6 +244,39 @@ __device__ __forceinline__ void set_bit(unsigned long long* X, int v) {
     if (q == (v >> 6)) X[q] |= 1ull << (v & 63);
 }
 
+// X &= ~row over the words of X that can be non-zero: from q0 (X is zero below word q0) up to
+// wa (the candidate count's words).  A store row is 16-byte aligned (W >= 2), so it is read
+// two words per load and only the pairs that overlap [q0, wa) are read.
+template <int W>
+__device__ __forceinline__ void andnot_live(unsigned long long* X, const unsigned long long* row,
+                                            int q0, int wa) {
+  static_assert(W % 2 == 0, "paired row loads need an even word count");
+#pragma unroll
+  for (int q = 0; q < W; q += 2)
+    if (q + 1 >= q0 && q < wa) {
+      const ulonglong2 r = *reinterpret_cast<const ulonglong2*>(row + q);
+      X[q] &= ~r.x;
+      X[q + 1] &= ~r.y;
+    }
+}
+
+// out = a & row over words [0, wa) (the words at and above wa are zero in a), paired loads.
+template <int W>
+__device__ __forceinline__ void and_live(unsigned long long* out, const unsigned long long* a,
+                                         const unsigned long long* row, int wa) {
+  static_assert(W % 2 == 0, "paired row loads need an even word count");
+#pragma unroll
+  for (int q = 0; q < W; q += 2)
+    if (q < wa) {
+      const ulonglong2 r = *reinterpret_cast<const ulonglong2*>(row + q);
+      out[q] = a[q] & r.x;
+      out[q + 1] = a[q + 1] & r.y;
+    } else {
+      out[q] = 0ull;
+      out[q + 1] = 0ull;
+    }
+}
+
 // ---------------------------------------------------------------------------------------------
 // Dense records (64 < |P| <= 512) are searched through a global task queue.  The warp that
 // dequeues such a record builds its adjacency bitmap once and stores it, with the vertex of
@@ -358,9 +391,8 @@ __device__ void dense_node(const Ctx& cx, const WideStore& ws, int slot, int dep
         for (int q = 0; q < W; ++q) cls[q] = left[q];
         int v;
         while ((v = lowest<W>(cls, wa)) >= 0) {
-#pragma unroll
-          for (int q = 0; q < W; ++q) cls[q] &= ~rows[v * W + q];
-          my_words += wa;
+          andnot_live<W>(cls, rows + v * W, v >> 6, wa);
+          my_words += wa - (v >> 6);
           clear_bit<W>(cls, v);
           clear_bit<W>(left, v);
           f(v, c, prefix);
@@ -468,9 +500,8 @@ __device__ void dense_node(const Ctx& cx, const WideStore& ws, int slot, int dep
           for (int q = 0; q < W; ++q) cls[q] = R[q];
           int v;
           while ((v = lowest<W>(cls, wa)) >= 0) {
-            my_words += wa;
-#pragma unroll
-            for (int q = 0; q < W; ++q) cls[q] &= ~rows[v * W + q];
+            my_words += wa - (v >> 6);
+            andnot_live<W>(cls, rows + v * W, v >> 6, wa);
             clear_bit<W>(cls, v);
             clear_bit<W>(R, v);
           }
@@ -506,8 +537,8 @@ __device__ void dense_node(const Ctx& cx, const WideStore& ws, int slot, int dep
         for (int q = 0; q < W; ++q) {
           stkR[depth][q] = R[q];
           stkP[depth][q] = rem[q];
-          Pn[q] = rem[q] & rows[u * W + q];
         }
+        and_live<W>(Pn, rem, rows + u * W, wa);
         my_words += wa;
         if (cx.maximal) {
           unsigned long long xs[W];
@@ -534,7 +565,7 @@ __device__ void dense_node(const Ctx& cx, const WideStore& ws, int slot, int dep
 
 // One lane per task (dynamic assignment).
 template <int W>
-__global__ void __launch_bounds__(128) k_clique_tasks(Ctx cx, WideStore ws,
+__global__ void __launch_bounds__(128, 5) k_clique_tasks(Ctx cx, WideStore ws,
                                                       const WTask* __restrict__ in, int64_t nin,
                                                       unsigned long long* next) {
   unsigned long long my_exp = 0, my_pruned = 0, my_words = 0;
