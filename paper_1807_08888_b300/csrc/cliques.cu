@@ -260,6 +260,38 @@ __device__ __forceinline__ void andnot_live(unsigned long long* X, const unsigne
     }
 }
 
+// One greedy colour class: the members of cls, taken in index order, that have no neighbour
+// among the members taken before them; each member also leaves R.  The class is built word
+// by word (unrolled, so every mask index is a compile-time constant): when word q is reached,
+// the words below it are already empty, so a member's row is applied from its own word pair
+// on.  cls is empty on return.
+template <int W>
+__device__ __forceinline__ void colour_class(unsigned long long* cls, unsigned long long* R,
+                                             const unsigned long long* rows, int wa,
+                                             unsigned long long& my_words) {
+  static_assert(W % 2 == 0, "paired row loads need an even word count");
+#pragma unroll
+  for (int q = 0; q < W; ++q) {
+    if (q < wa) {
+      while (cls[q]) {
+        const int b = __ffsll((long long)cls[q]) - 1;
+        const unsigned long long bit = 1ull << b;
+        cls[q] &= ~bit;
+        R[q] &= ~bit;
+        const unsigned long long* row = rows + (int64_t)(q * 64 + b) * W;
+#pragma unroll
+        for (int r = q & ~1; r < W; r += 2)
+          if (r < wa) {
+            const ulonglong2 x = *reinterpret_cast<const ulonglong2*>(row + r);
+            cls[r] &= ~x.x;
+            cls[r + 1] &= ~x.y;
+          }
+        my_words += wa - q;
+      }
+    }
+  }
+}
+
 // out = a & row over words [0, wa) (the words at and above wa are zero in a), paired loads.
 template <int W>
 __device__ __forceinline__ void and_live(unsigned long long* out, const unsigned long long* a,
@@ -498,13 +530,7 @@ __device__ void dense_node(const Ctx& cx, const WideStore& ws, int slot, int dep
           unsigned long long cls[W];
 #pragma unroll
           for (int q = 0; q < W; ++q) cls[q] = R[q];
-          int v;
-          while ((v = lowest<W>(cls, wa)) >= 0) {
-            my_words += wa - (v >> 6);
-            andnot_live<W>(cls, rows + v * W, v >> 6, wa);
-            clear_bit<W>(cls, v);
-            clear_bit<W>(R, v);
-          }
+          colour_class<W>(cls, R, rows, wa, my_words);
         }
         if (!any<W>(R, wa)) {
           ++my_pruned;
