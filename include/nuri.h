@@ -42,7 +42,7 @@ typedef int32_t nuri_status;
 #define NURI_OK 0
 #define NURI_ERR_INVALID 1   /* bad argument: k < 1, id out of range, bad query, ...      */
 #define NURI_ERR_OOM 2       /* device or pinned-host allocation failed                    */
-#define NURI_ERR_LIMIT 3     /* a built-in size limit was exceeded (clique size > 128, ...) */
+#define NURI_ERR_LIMIT 3     /* a built-in size limit was exceeded (clique size > 256, ...) */
 #define NURI_ERR_TIMEOUT 4   /* the query ran past its time budget (nuri_set_time_budget)  */
 #define NURI_ERR_CANCELLED 5 /* the request was cancelled                                  */
 #define NURI_ERR_CUDA 6      /* a CUDA runtime call failed                                 */
@@ -161,7 +161,7 @@ nuri_status nuri_graph_get_info(const nuri_graph* g, nuri_graph_info* info);
  *          NURI_CLIQUE_MAXIMAL; optionally NURI_KEEP_TIES, NURI_NO_PRUNE
  *   frontier_cap  maximum number of frontier records kept on the device before the lowest
  *          buckets are spilled to pinned host memory (0 = library default)
- * Errors: NURI_ERR_INVALID, NURI_ERR_LIMIT (a clique larger than 128), NURI_ERR_OOM, CUDA.
+ * Errors: NURI_ERR_INVALID, NURI_ERR_LIMIT (a clique larger than 256), NURI_ERR_OOM, CUDA.
  */
 nuri_status nuri_topk_cliques(nuri_graph* g, int32_t k, int32_t rank, uint32_t flags,
                               int64_t frontier_cap, void* stream, nuri_result** out);

@@ -43,7 +43,7 @@
 namespace nuri {
 namespace {
 
-constexpr int MAXD = 128;      // largest clique the records can hold
+constexpr int MAXD = 256;      // largest clique the records can hold
 constexpr int NB = 256;        // frontier buckets (bucket NB-1 holds every bound >= NB-1;
                                // cliques never exceed MAXD < NB-1, so the order is exact)
 constexpr int PSMEM = 512;     // P entries staged in shared memory per warp

@@ -210,22 +210,22 @@ def test_edge_cases():
 
 
 def test_clique_limit_is_reported():
-    # a 129-clique exceeds the 128-vertex record limit: NURI_ERR_LIMIT, graph still usable
-    c = list(range(129))
+    # a 257-clique exceeds the 256-vertex record limit: NURI_ERR_LIMIT, graph still usable
+    c = list(range(257))
     e = np.array(list(itertools.combinations(c, 2)), np.int32)
-    G = nuri.load_graph(129, e[:, 0].copy(), e[:, 1].copy())
+    G = nuri.load_graph(257, e[:, 0].copy(), e[:, 1].copy())
     with pytest.raises(nuri.NuriError) as ei:
         nuri.topk_cliques(G, 1)
     assert ei.value.code == nuri.ERR_LIMIT
     G2 = nuri.load_graph(4, np.array([0, 1], np.int32), np.array([1, 2], np.int32))
     assert nuri.topk_cliques(G2, 1)[0] == (2, (0, 1))
-    # a 100-clique is within the limit
-    c = list(range(100))
+    # a 200-clique is within the limit
+    c = list(range(200))
     e = np.array(list(itertools.combinations(c, 2)), np.int32)
-    G3 = nuri.load_graph(100, e[:, 0].copy(), e[:, 1].copy())
+    G3 = nuri.load_graph(200, e[:, 0].copy(), e[:, 1].copy())
     r = nuri.topk_cliques(G3, 3)
-    assert [x[0] for x in r] == [100, 99, 99]
-    assert r[0][1] == tuple(c) and r[1][1] == tuple(c[:99])
+    assert [x[0] for x in r] == [200, 199, 199]
+    assert r[0][1] == tuple(c) and r[1][1] == tuple(c[:199])
 
 
 def test_device_input_tensors():
