@@ -44,8 +44,8 @@ namespace nuri {
 namespace {
 
 constexpr int MAXD = 256;      // largest clique the records can hold
-constexpr int NB = 256;        // frontier buckets (bucket NB-1 holds every bound >= NB-1;
-                               // cliques never exceed MAXD < NB-1, so the order is exact)
+constexpr int NB = 1024;       // frontier buckets by bound (bucket NB-1 holds every bound
+                               // >= NB-1; cliques never exceed MAXD < NB-1)
 constexpr int PSMEM = 512;     // P entries staged in shared memory per warp
 
 struct Rec {
@@ -146,6 +146,18 @@ __device__ __forceinline__ bool past_deadline(const Ctx& cx) {
   return global_ns() > *(const volatile uint64_t*)cx.deadline;
 }
 
+// Largest s with C(c, s) >= k (0 when there is none): a clique of size c holds that many
+// cliques of size s, so the k-th best clique size is at least s.
+__device__ __forceinline__ int subset_tau(int c, int k) {
+  double b = 1.0;  // C(c, s)
+  int s = c;
+  while (s > 1 && b < (double)k) {
+    b = b * s / (double)(c - s + 1);
+    --s;
+  }
+  return b >= (double)k ? s : 0;
+}
+
 // Append one clique (ranks) of size c as a candidate result and refresh tau.
 __device__ void add_result(const Ctx& cx, const int32_t* V, int nv, int32_t extra_count,
                            const int32_t* extra) {
@@ -162,14 +174,9 @@ __device__ void add_result(const Ctx& cx, const int32_t* V, int nv, int32_t extr
   if (c > ld_volatile(&cx.st->hmax)) atomicMax(&cx.st->hmax, c);
   if (!cx.maximal && c > ld_volatile(&cx.st->tau)) {
     // every subset of a clique is a clique: one of size c holds C(c, s) cliques of size s, so
-    // the k-th best size is at least the largest s with C(c, s) >= k
-    double b = 1.0;  // C(c, s)
-    int s = c;
-    while (s > 1 && b < (double)cx.k) {
-      b = b * s / (double)(c - s + 1);
-      --s;
-    }
-    if (b >= (double)cx.k && s > ld_volatile(&cx.st->tau)) atomicMax(&cx.st->tau, s);
+    // the k-th best size is at least the largest such s with C(c, s) >= k
+    const int s = subset_tau(c, cx.k);
+    if (s > ld_volatile(&cx.st->tau)) atomicMax(&cx.st->tau, s);
   }
   if ((int64_t)(slot + 1) < (int64_t)cx.k) return;  // fewer than k results so far
   publish_threshold(cx.st->hist, ld_volatile(&cx.st->hmax), 0, cx.k, &cx.st->tau);
@@ -1323,18 +1330,87 @@ __global__ void k_stage_hist(const Rec* stage, int64_t cnt, int32_t* hist) {
     if (stage[i].nv > 0) atomicAdd(&hist[bucket_of(stage[i].bound)], 1);
 }
 
+// Warm start for tau (all-cliques ranking): one warp per seed grows a clique greedily inside
+// the seed's candidates (always adding the candidate of largest degree, then keeping the
+// candidates adjacent to it) and publishes subset_tau of its size.  The cliques themselves
+// are not recorded (the search finds them again); only the lower bound on the k-th best is
+// used, so the answer is unchanged.  buf: max_out entries per warp.
+__global__ void k_greedy_tau(DevGraph g, const int32_t* __restrict__ seeds, int64_t nseeds,
+                             int32_t k, int32_t* __restrict__ buf, int32_t* __restrict__ tau) {
+  const int lane = threadIdx.x & 31;
+  const unsigned FULL = 0xffffffffu;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  int32_t* P = buf + warp * (int64_t)g.max_out;
+  for (int64_t i = warp; i < nseeds; i += nwarps) {
+    const int32_t v = seeds[i];
+    const int64_t b = g.ooff[v];
+    int p = (int)(g.ooff[v + 1] - b);
+    for (int t = lane; t < p; t += 32) P[t] = g.oout[b + t];
+    __syncwarp();
+    int c = 1;
+    while (p > 0) {
+      // the candidate of largest degree (ties: lowest rank)
+      int best = -1, bestd = -1;
+      for (int t = lane; t < p; t += 32) {
+        const int32_t d = __ldg(g.deg + __ldg(g.vert_of + P[t]));
+        if (d > bestd) {
+          bestd = d;
+          best = P[t];
+        }
+      }
+      for (int o = 16; o; o >>= 1) {
+        const int od = __shfl_xor_sync(FULL, bestd, o);
+        const int ob = __shfl_xor_sync(FULL, best, o);
+        if (od > bestd || (od == bestd && ob >= 0 && (best < 0 || ob < best))) {
+          bestd = od;
+          best = ob;
+        }
+      }
+      const int32_t u = best;
+      ++c;
+      // keep the candidates adjacent to u (in place: writes never pass the reads)
+      int cnt = 0;
+      for (int base = 0; base < p; base += 32) {
+        const int t = base + lane;
+        bool keep = false;
+        int32_t x = 0;
+        if (t < p) {
+          x = P[t];
+          if (x != u)
+            keep = x > u ? contains64(g.oout, g.ooff[u], g.ooff[u + 1], x)
+                         : contains64(g.oout, g.ooff[x], g.ooff[x + 1], u);
+        }
+        const unsigned bal = __ballot_sync(FULL, keep);
+        __syncwarp();
+        if (keep) P[cnt + __popc(bal & ((1u << lane) - 1))] = x;
+        cnt += __popc(bal);
+        __syncwarp();
+      }
+      p = cnt;
+      if (c >= MAXD) break;
+    }
+    if (lane == 0) {
+      const int st = subset_tau(c, k);
+      if (st > 0) atomicMax(tau, st);
+    }
+    __syncwarp();
+  }
+}
+
 struct BucketPtrs {
   Rec* base[NB];
   int64_t fill[NB];  // current counts before the scatter
 };
 
-__global__ void k_stage_scatter(const Rec* stage, int64_t cnt, BucketPtrs bp, int32_t* cursor) {
+__global__ void k_stage_scatter(const Rec* stage, int64_t cnt, const BucketPtrs* __restrict__ bp,
+                                int32_t* cursor) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt;
        i += (int64_t)gridDim.x * blockDim.x) {
     if (stage[i].nv <= 0) continue;
     int b = bucket_of(stage[i].bound);
-    int64_t pos = bp.fill[b] + atomicAdd(&cursor[b], 1);
-    bp.base[b][pos] = stage[i];
+    int64_t pos = bp->fill[b] + atomicAdd(&cursor[b], 1);
+    bp->base[b][pos] = stage[i];
   }
 }
 
@@ -1487,6 +1563,10 @@ struct ResultStore {
 // overflow the set with cliques that tau has since passed.  A set that has already
 // overflowed (rows lost) is left alone: the pass is then re-run with the final tau.
 void compact_results(Ctx& cx, ResultStore& rs, cudaStream_t s) {
+  // a caller's copy of the context may predate a compaction made further down: take the
+  // current buffer first, whatever happens below
+  cx.res = rs.buf.p;
+  cx.res_cap = rs.cap;
   int64_t rc = 0;
   int32_t tau = 0;
   NURI_CUDA(cudaMemcpyAsync(&rc, &cx.st->res_count, 8, cudaMemcpyDeviceToHost, s));
@@ -1691,6 +1771,7 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
   int32_t tau_init = INT32_MIN;
   int restarts = 0;
   std::vector<HostBucket> buckets(NB);
+  DBuf<BucketPtrs> bp_dev;  // the bucket table of a scatter (16 KB, passed through memory)
 
   // seeds: sorted by bound descending
   DBuf<int32_t> skeys, svals, skeys2, svals2, bhist;
@@ -1727,6 +1808,33 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
         pos += seed_hist[c * NB + b];
         seed_hi[c * NB + b] = pos;
       }
+  }
+
+  // warm start: greedy cliques from the highest-bound seeds of each class lift tau before the
+  // search (all-cliques ranking with pruning only)
+  if (!maximal && !no_prune && n > 0 && k > 0) {
+    DBuf<int32_t> gbuf, gtau;
+    const int gblocks = sm_count() * 4;  // 8 warps each
+    gbuf.alloc((int64_t)gblocks * 8 * std::max(g.max_out, 1), s);
+    gtau.alloc(1, s);
+    const int32_t neg = INT32_MIN;
+    NURI_CUDA(cudaMemcpyAsync(gtau.p, &neg, 4, cudaMemcpyHostToDevice, s));
+    const int64_t c0 = seed_lo[NB - 1], n0 = seed_hi[0] - c0;  // class 0 (wide) seeds
+    const int64_t n1 = seed_hi[NB];                             // class 1 (narrow) seeds
+    const int64_t take0 = std::min<int64_t>(n0, 4096), take1 = std::min<int64_t>(n1, 1024);
+    if (take0 > 0) {
+      ++launches;
+      k_greedy_tau<<<gblocks, 256, 0, s>>>(g, svals2.p + c0, take0, k, gbuf.p, gtau.p);
+    }
+    if (take1 > 0) {
+      ++launches;
+      k_greedy_tau<<<gblocks, 256, 0, s>>>(g, svals2.p, take1, k, gbuf.p, gtau.p);
+    }
+    NURI_CUDA(cudaGetLastError());
+    int32_t gt = INT32_MIN;
+    NURI_CUDA(cudaMemcpyAsync(&gt, gtau.p, 4, cudaMemcpyDeviceToHost, s));
+    NURI_CUDA(cudaStreamSynchronize(s));
+    tau_init = std::max(tau_init, gt);
   }
 
   QState hs;
@@ -1937,7 +2045,9 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
         }
         NURI_CUDA(cudaMemsetAsync(bhist.p, 0, sizeof(int32_t) * NB, s));
         ++launches;
-        k_stage_scatter<<<grid_for(cnt), 256, 0, s>>>(arr, cnt, bp, bhist.p);
+        if (!bp_dev.p) bp_dev.alloc(1, s);
+        NURI_CUDA(cudaMemcpyAsync(bp_dev.p, &bp, sizeof(BucketPtrs), cudaMemcpyHostToDevice, s));
+        k_stage_scatter<<<grid_for(cnt), 256, 0, s>>>(arr, cnt, bp_dev.p, bhist.p);
         ++launches;
         k_clear_stage<<<grid_for(cnt), 256, 0, s>>>(arr, cnt);
         for (int b = 0; b < NB; ++b) buckets[b].count += sh[b];
