@@ -513,8 +513,8 @@ __device__ void dense_node(const Ctx& cx, const WideStore& ws, int slot, int dep
             for (int q = 0; q <= l; ++q) t->picks[q] = pick[q];
 #pragma unroll
             for (int q = 0; q < KWIDE; ++q) {
-              t->P[q] = q < W ? PL[q] : 0ull;
-              if (cx.maximal) t->X[q] = q < W ? XL[q] : 0ull;
+              t->P[q] = q < wa ? PL[q] : 0ull;
+              if (cx.maximal) t->X[q] = q < wa ? XL[q] : 0ull;
             }
           }
           return;
@@ -545,44 +545,40 @@ __device__ void dense_node(const Ctx& cx, const WideStore& ws, int slot, int dep
         }
       }
       if (level_ok) {
+        // the stack keeps only the record's live words (q < wa); reads mask the rest
 #pragma unroll
-        for (int q = 0; q < W; ++q) {
-          stkP[depth][q] = Pn[q];
-          stkR[depth][q] = R[q];
-        }
+        for (int q = 0; q < W; ++q)
+          if (q < wa) {
+            stkP[depth][q] = Pn[q];
+            stkR[depth][q] = R[q];
+          }
         if (cx.maximal)
 #pragma unroll
-          for (int q = 0; q < W; ++q) stkX[depth][q] = Xn[q];
+          for (int q = 0; q < W; ++q)
+            if (q < wa) stkX[depth][q] = Xn[q];
       }
     }
     if (level_ok) {
       unsigned long long R[W];
 #pragma unroll
-      for (int q = 0; q < W; ++q) R[q] = stkR[depth][q];
+      for (int q = 0; q < W; ++q) R[q] = q < wa ? stkR[depth][q] : 0ull;
       const int u = highest<W>(R, wa);
       if (u >= 0) {
+        // branching on u changes one word of the level: write only that word back
+        const int qu = u >> 6;
+        const unsigned long long ubit = 1ull << (u & 63);
+        stkR[depth][qu] &= ~ubit;
+        stkP[depth][qu] &= ~ubit;
         unsigned long long rem[W];
 #pragma unroll
-        for (int q = 0; q < W; ++q) rem[q] = stkP[depth][q];
-        clear_bit<W>(R, u);
-        clear_bit<W>(rem, u);
-#pragma unroll
-        for (int q = 0; q < W; ++q) {
-          stkR[depth][q] = R[q];
-          stkP[depth][q] = rem[q];
-        }
+        for (int q = 0; q < W; ++q) rem[q] = q < wa ? stkP[depth][q] : 0ull;
         and_live<W>(Pn, rem, rows + u * W, wa);
         my_words += wa;
         if (cx.maximal) {
-          unsigned long long xs[W];
 #pragma unroll
-          for (int q = 0; q < W; ++q) {
-            xs[q] = stkX[depth][q];
-            Xn[q] = xs[q] & rows[u * W + q];
-          }
-          set_bit<W>(xs, u);
-#pragma unroll
-          for (int q = 0; q < W; ++q) stkX[depth][q] = xs[q];
+          for (int q = 0; q < W; ++q)
+            Xn[q] = q < wa ? (stkX[depth][q] & rows[u * W + q]) : 0ull;
+          stkX[depth][qu] |= ubit;
         }
         ++depth;
         pick[depth] = (uint16_t)u;
