@@ -67,7 +67,7 @@ typedef int32_t nuri_status;
 
 typedef struct nuri_graph nuri_graph;
 
-/* Counters of one query.  "expansions" counts child subgraphs created (Algorithm 1 line 14;
+/* Counters of one query.  "expansions" counts child subgraphs created (Algorithm 1;
  * for patterns, extension candidates examined), including children pruned at once. */
 typedef struct nuri_stats {
   int64_t expansions;      /* children created                                   */

@@ -102,7 +102,7 @@ typedef struct orc_result {
   int32_t* edge_off;
   int32_t* edges;
   int32_t* labels;
-  int64_t expansions;   // children created (Alg.1 line 14 / Alg.2 line 21 granularity)
+  int64_t expansions;   // children created (one per extension of Algorithm 1 / Algorithm 2)
   int64_t dequeued;     // subgraphs / groups removed from Q
   int64_t pruned;       // children dropped by dominated()
   int32_t complete;     // 0 when a work budget stopped the run early
@@ -165,10 +165,10 @@ double now_s() {
       .count();
 }
 
-// ---- the top-k result set R of Algorithm 1 (lines 6-10) ------------------------------------
+// ---- the top-k result set R of Algorithm 1 ----------------------------------------------------
 // Entries are kept with their score.  k-th(R) is the k-th largest score among the entries.
-// Insertion follows line 7 (|R| < k or score >= k-th); after an insertion that makes |R| > k,
-// every entry with a score below the new k-th score is removed (lines 9-10), so ties with the
+// An entry is inserted when |R| < k or its score >= k-th; after an insertion that makes |R| > k,
+// every entry with a score below the new k-th score is removed, so ties with the
 // k-th entry stay and |R| may exceed k.
 template <class Entry>
 struct ResultSet {
@@ -261,7 +261,7 @@ extern "C" int orc_topk_cliques(int32_t n, int64_t m, const int32_t* src, const 
     }
     Q.push({(int64_t)store[slot].V.size(), (int64_t)store[slot].P.size(), seq++, slot});
   };
-  // Algorithm 1, lines 1-3: one unit subgraph per vertex.
+  // Algorithm 1, initialisation: one unit subgraph per vertex.
   for (int v = 0; v < n; ++v) {
     CliqueSub s;
     s.V = {v};
@@ -272,8 +272,8 @@ extern "C" int orc_topk_cliques(int32_t n, int64_t m, const int32_t* src, const 
   ResultSet<vector<int>> R(k);
   int64_t expansions = 0, dequeued = 0, pruned = 0;
   int complete = 1;
-  while (!Q.empty()) {                        // line 4
-    QE top = Q.top();                         // line 5
+  while (!Q.empty()) {                        // until the queue is empty
+    QE top = Q.top();                         // dequeue the highest priority
     Q.pop();
     CliqueSub s = std::move(store[top.idx]);
     free_slots.push_back(top.idx);
@@ -281,20 +281,20 @@ extern "C" int orc_topk_cliques(int32_t n, int64_t m, const int32_t* src, const 
     int64_t score = (int64_t)s.V.size();
     bool relevant = true;
     if (maximal_only) relevant = common_nbrs_all(g, s.V).empty();
-    if (relevant) R.offer(score, s.V);        // lines 6-10
-    // line 11: expand unless dominated by the k-th entry
+    if (relevant) R.offer(score, s.V);        // result-set update
+    // expand unless dominated by the k-th entry
     if (!R.full() || !((int64_t)(s.V.size() + s.P.size()) < R.kth())) {
-      for (size_t j = 0; j < s.P.size(); ++j) {  // line 12: neighbouring vertices d
-        int d = s.P[j];                           // line 13: expandable(s, d) = d in P_s
-        CliqueSub c;                              // line 14
+      for (size_t j = 0; j < s.P.size(); ++j) {  // neighbouring vertices d
+        int d = s.P[j];                           // expandable(s, d) = d in P_s
+        CliqueSub c;                              // the child s + d
         c.V = s.V;
         c.V.push_back(d);
         for (size_t t = j + 1; t < s.P.size(); ++t)
           if (g.has(d, s.P[t])) c.P.push_back(s.P[t]);
         ++expansions;
-        // line 15: dominated(s', k-th(R))
+        // dominated(s', k-th(R))
         if (!R.full() || !((int64_t)(c.V.size() + c.P.size()) < R.kth()))
-          enqueue(std::move(c));                  // line 16
+          enqueue(std::move(c));                  // enqueue the child
         else
           ++pruned;
       }
@@ -691,7 +691,7 @@ extern "C" int orc_topk_iso(int32_t n, int64_t m, const int32_t* src, const int3
       }
       continue;
     }
-    if (R.full() && s.bound < R.kth()) continue;  // line 11
+    if (R.full() && s.bound < R.kth()) continue;  // dominated: no expansion
     int q = order[s.depth];
     int pidx = -1;
     for (int i = 0; i < s.depth; ++i)
@@ -926,7 +926,7 @@ extern "C" int orc_topk_patterns(int32_t n, int64_t m, const int32_t* src, const
   int64_t seq = 0, expansions = 0, dequeued = 0, pruned = 0;
   ResultSet<vector<int>> R(k);  // entries: canonical codes
   std::map<vector<int>, Pat> pat_of;
-  // Alg.2 lines 1-8: one group per 1-edge pattern present in the graph
+  // Algorithm 2, initialisation: one group per 1-edge pattern present in the graph
   {
     std::set<std::pair<int, int>> lp;
     for (int v = 0; v < n; ++v)
@@ -956,9 +956,9 @@ extern "C" int orc_topk_patterns(int32_t n, int64_t m, const int32_t* src, const
       pat_of[code] = S.p;
       R.offer(S.f, code);
     }
-    if (R.full() && S.f < R.kth()) continue;  // line 16
+    if (R.full() && S.f < R.kth()) continue;  // dominated: no expansion
     if (mS >= M) continue;                     // expandable() is false for every member
-    // lines 17-24: child groups
+    // child groups: patterns with one more edge
     vector<Pat> kids;
     for (int i = 0; i < S.p.nv; ++i) {
       if (S.p.nv < 8)
@@ -985,7 +985,7 @@ extern "C" int orc_topk_patterns(int32_t n, int64_t m, const int32_t* src, const
       int64_t f = mni(g, c);
       if (f == 0) continue;  // no member subgraph: no group
       ++expansions;
-      // lines 25-27
+      // enqueue the child group
       if (!R.full() || !(f < R.kth())) {
         store.push_back({c, f});
         Q.push({(int64_t)c.E.size(), f, seq++, (int32_t)store.size() - 1});

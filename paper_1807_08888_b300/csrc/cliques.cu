@@ -11,7 +11,7 @@
 //   tau        = k-th best size among results found so far (global, atomicMax, monotone)
 //
 // Work is organised as a bucketed best-first frontier driven from the host:
-//   * seeds (one per vertex, Alg.1 lines 1-3) are sorted by bound and consumed in
+//   * seeds (one per vertex, Algorithm 1's initialisation) are sorted by bound and consumed in
 //     descending-bound chunks; frontier records live in 256 buckets keyed by bound (LIFO
 //     inside a bucket, so the deepest records of the best bound go first);
 //   * each round takes the highest bucket (or seed chunk) whose bound >= tau and expands it
@@ -733,7 +733,7 @@ __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
       }
     }
 
-    // ---- dequeue: prune (line 11), then result insertion (lines 6-10) ----
+    // ---- dequeue: prune (dominated), then result insertion ----
     int32_t tau = ld_volatile(&cx.st->tau);
     int bound = nv + p;
     if (!cx.no_prune && bound < tau) {

@@ -16,7 +16,7 @@
 //     the tree parent and hop of every position, back edges, and the symmetry-breaking
 //     constraints (automorphisms by backtracking over <= 8! label-preserving permutations;
 //     orbit-stabiliser chain);
-//   * seeds (Alg.1 lines 1-3): every data vertex with the root's label, for every query, with
+//   * seeds (Algorithm 1, initialisation): every data vertex with the root's label, for every query, with
 //     its bound score(v) + u; all seeds of all queries are sorted by bound, descending;
 //   * k_iso_search: one warp per seed, dynamic assignment in bound order; the warp runs a
 //     depth-first search over the matching order.  Candidates of a level come from the

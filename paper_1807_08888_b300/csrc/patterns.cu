@@ -449,7 +449,7 @@ void topk_patterns(nuri_graph* G, int32_t M, int32_t k, uint32_t flags, cudaStre
     return (int64_t)std::min(cnt[(size_t)a * L + b], cnt[(size_t)b * L + a]);
   };
 
-  // result set R (Algorithm 2 lines 11-15): entries (f, code, pattern)
+  // result set R (Algorithm 2): entries (f, code, pattern)
   struct REntry {
     int64_t f;
     Code code;
@@ -486,7 +486,7 @@ void topk_patterns(nuri_graph* G, int32_t M, int32_t k, uint32_t flags, cudaStre
   Pool pool;
   pool.init(words, 64, s);
 
-  // seeds (Algorithm 2 lines 1-8): one group per 1-edge pattern present
+  // seeds (Algorithm 2, initialisation): one group per 1-edge pattern present
   for (int a = 0; a < L; ++a)
     for (int b = a; b < L; ++b) {
       int64_t f = f1(a, b);
@@ -562,7 +562,7 @@ void topk_patterns(nuri_graph* G, int32_t M, int32_t k, uint32_t flags, cudaStre
       store[si].dom[0] = -1;
       continue;
     }
-    // ---- expand the group: child patterns by one more edge (lines 17-24) ----
+    // ---- expand the group: child patterns by one more edge ----
     ensure_domains(S);
     struct Child {
       Pat p;
@@ -724,7 +724,7 @@ void topk_patterns(nuri_graph* G, int32_t M, int32_t k, uint32_t flags, cudaStre
           continue;
         }
         store.push_back(kg[c]);
-        Q.push((int)store.size() - 1);  // lines 25-27
+        Q.push((int)store.size() - 1);  // enqueue the child group
       }
       NURI_CUDA(cudaStreamSynchronize(s));
     }

@@ -1,5 +1,5 @@
 // Device helpers shared by the query engines: the global k-th-best threshold and result
-// appends (Algorithm 1 lines 6-10 and the dominated() test of lines 11 and 15).
+// appends (Algorithm 1's result-set update and its dominated() test).
 #pragma once
 
 #include <cuda_runtime.h>
