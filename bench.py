@@ -264,7 +264,10 @@ def main():
     roof_tail = {"bound": "alu", "kernel": "k_clique_tasks<8>", "achieved": tach,
                  "peak": apeak, "unit": "Gword-ops/s", "frac": tach / apeak,
                  "peak_source": "derived: 148 SMs x 32 64-bit logical ops/clk x sm_max_mhz",
-                 "traffic": traffic.get("k_clique_tasks_chunglu1m"),
+                 # DRAM bytes of one captured wave (ncu); its duration beside it
+                 "traffic": (traffic.get("k_clique_tasks_chunglu1m") or {}).get("dram_bytes"),
+                 "traffic_launch_ms": (traffic.get("k_clique_tasks_chunglu1m") or {}).get(
+                     "launch_ms"),
                  "algorithmic_words_per_launch": tail_words / max(tail_launches, 1),
                  "avg_launch_ms": tail_ms / max(tail_launches, 1),
                  "share_of_step": tail_ms / total_ms}
