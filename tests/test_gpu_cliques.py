@@ -281,3 +281,9 @@ def test_chung_lu_config_properties(monkeypatch):
     again = [(r[0], r[1]) for r in nuri.topk_cliques(G, 100)]
     monkeypatch.delenv("NURI_TASK_SPLIT")
     assert again == got
+    # a small result set is compacted many times, also between the 4-word and 8-word tiers of
+    # one round (the set is replaced while the round is running): same list
+    monkeypatch.setenv("NURI_RESULT_CAP", "256")
+    small = nuri.topk_cliques(G, 100)
+    monkeypatch.delenv("NURI_RESULT_CAP")
+    assert [(r[0], r[1]) for r in small] == got
