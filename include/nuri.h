@@ -236,6 +236,20 @@ nuri_status nuri_hop_index_noalloc(int32_t n, const int64_t* off, const int32_t*
                                    void* stream);
 
 /*
+ * nuri_tune_cliques -- autotune the dense-record search of top-k clique queries on this graph
+ * (the batched form's work granularity; no counterpart in the paper, whose search is
+ * sequential).  Runs the query (g, k, flags) once per candidate task granularity (48, 96,
+ * 128, 192: search nodes with more candidates than this become tasks of the global queue),
+ * times each with the device timer and keeps the fastest for every later nuri_topk_cliques
+ * call on g.  Results never depend on the setting.  *chosen (may be NULL) receives it and
+ * *best_ms (may be NULL) its device time.  The environment variable NURI_TASK_SPLIT, when
+ * set, still overrides the tuned value.  Errors: those of nuri_topk_cliques (the previous
+ * setting is kept).
+ */
+nuri_status nuri_tune_cliques(nuri_graph* g, int32_t k, uint32_t flags, void* stream,
+                              int32_t* chosen, double* best_ms);
+
+/*
  * nuri_set_time_budget -- limit the device time of every later query on any graph: a query
  * whose kernels run past `ms` milliseconds stops and returns NURI_ERR_TIMEOUT (the graph
  * stays usable).  The check reads the GPU's global timer inside the search loops; no kernel

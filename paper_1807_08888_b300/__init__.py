@@ -20,7 +20,7 @@ import numpy as np
 
 __all__ = [
     "NuriError", "lib", "load_graph", "Graph", "topk_cliques", "topk_iso", "topk_iso_batch",
-    "topk_patterns", "hop_index", "hop_index_noalloc", "set_time_budget", "Server", "Result", "LIB_PATH", "EXPORTS",
+    "topk_patterns", "hop_index", "hop_index_noalloc", "set_time_budget", "tune_cliques", "Server", "Result", "LIB_PATH", "EXPORTS",
     "RANK_SIZE", "RANK_WEIGHT_SUM", "RANK_DEGREE_SUM", "RANK_MNI",
 ]
 
@@ -40,6 +40,7 @@ EXPORTS = (
     "nuri_topk_iso", "nuri_topk_iso_batch", "nuri_topk_patterns", "nuri_hop_index",
     "nuri_hop_index_noalloc",
     "nuri_free_result", "nuri_last_error", "nuri_version", "nuri_set_time_budget",
+    "nuri_tune_cliques",
     "nuri_server_create", "nuri_server_submit", "nuri_server_poll", "nuri_server_wait",
     "nuri_server_stats", "nuri_server_destroy",
 )
@@ -142,6 +143,9 @@ def lib():
             L.nuri_hop_index.restype = i32
             L.nuri_hop_index_noalloc.argtypes = [i32, P, P, i64, P, i32, P, i32, P, P]
             L.nuri_hop_index_noalloc.restype = i32
+            L.nuri_tune_cliques.argtypes = [P, i32, u32, P, ctypes.POINTER(i32),
+                                            ctypes.POINTER(ctypes.c_double)]
+            L.nuri_tune_cliques.restype = i32
             L.nuri_set_time_budget.argtypes = [ctypes.c_double]
             L.nuri_set_time_budget.restype = i32
             L.nuri_server_create.argtypes = [P, ctypes.POINTER(_ServerCfg),
@@ -402,6 +406,17 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def tune_cliques(g: Graph, k: int, maximal=False, stream=None):
+    """Autotune the dense clique search on g (nuri_tune_cliques): times one top-k query per
+    candidate task granularity and keeps the fastest for later queries on g.  Returns
+    (chosen granularity, its device ms)."""
+    c = ctypes.c_int32()
+    t = ctypes.c_double()
+    _check(lib().nuri_tune_cliques(g.handle, int(k), CLIQUE_MAXIMAL if maximal else 0,
+                                   _stream(stream), ctypes.byref(c), ctypes.byref(t)))
+    return int(c.value), float(t.value)
 
 
 def set_time_budget(ms: float) -> None:

@@ -121,6 +121,39 @@ nuri_status nuri_graph_get_info(const nuri_graph* g, nuri_graph_info* info) {
   });
 }
 
+nuri_status nuri_tune_cliques(nuri_graph* g, int32_t k, uint32_t flags, void* stream,
+                              int32_t* chosen, double* best_ms) {
+  return guarded([&] {
+    if (!g) NURI_FAIL(NURI_ERR_INVALID, "nuri_tune_cliques: NULL graph");
+    if (k < 1) NURI_FAIL(NURI_ERR_INVALID, "nuri_tune_cliques: k must be >= 1");
+    // candidate task granularities of the dense-record search (node size above which a
+    // node's children become tasks); each is timed on one query, the fastest is kept
+    static const int32_t cand[] = {48, 96, 128, 192};
+    int32_t best = 0;
+    double best_t = 0.0;
+    const int32_t before = g->clique_split_bits;
+    for (int32_t c : cand) {
+      g->clique_split_bits = c;
+      nuri_result* r = nullptr;
+      try {
+        topk_cliques(g, k, flags, 0, (cudaStream_t)stream, &r);
+      } catch (...) {
+        g->clique_split_bits = before;
+        throw;
+      }
+      const double t = r->stats.device_ms;
+      nuri_free_result(r);
+      if (best == 0 || t < best_t) {
+        best = c;
+        best_t = t;
+      }
+    }
+    g->clique_split_bits = best;
+    if (chosen) *chosen = best;
+    if (best_ms) *best_ms = best_t;
+  });
+}
+
 nuri_status nuri_topk_cliques(nuri_graph* g, int32_t k, int32_t rank, uint32_t flags,
                               int64_t frontier_cap, void* stream, nuri_result** out) {
   return guarded([&] {

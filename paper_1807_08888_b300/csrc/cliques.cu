@@ -594,7 +594,7 @@ __device__ void dense_node(const Ctx& cx, const WideStore& ws, int slot, int dep
 
 // One lane per task (dynamic assignment).
 template <int W>
-__global__ void __launch_bounds__(128, 5) k_clique_tasks(Ctx cx, WideStore ws,
+__global__ void __launch_bounds__(128, 6) k_clique_tasks(Ctx cx, WideStore ws,
                                                       const WTask* __restrict__ in, int64_t nin,
                                                       unsigned long long* next) {
   unsigned long long my_exp = 0, my_pruned = 0, my_words = 0;
@@ -1757,6 +1757,7 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
   if (g.max_out > PSMEM) pscratch.alloc((int64_t)total_warps * g.max_out, s);
   DBuf<Rec> stage, deferred, inbuf, wide, mid;
   DenseBufs dense;
+  if (G->clique_split_bits > 0) dense.split_bits = G->clique_split_bits;  // tuned per graph
   TailTime tail;
   stage.alloc(stage_cap, s);
   ++launches;

@@ -118,6 +118,7 @@ struct nuri_graph {
   nuri::DevGraph d;
   int64_t num_edges = 0, dropped = 0;
   int32_t degeneracy = -1;  // from the peeling order (-1: degree order used)
+  int32_t clique_split_bits = 0;  // dense-search task granularity chosen by nuri_tune_cliques
   cudaStream_t stream = nullptr;
   nuri::DBuf<int64_t> off, ooff, lsoff, lab_off;
   nuri::DBuf<int32_t> adj, deg, oout, vert_of, rank_of, weights, idx_w, idx_d, gmax_w, gmax_d;

@@ -191,6 +191,17 @@ def test_result_compaction_keeps_the_top_k(monkeypatch):
     assert [(r[0], r[1]) for r in got] == [(r[0], r[1]) for r in ref]
 
 
+def test_tune_cliques_keeps_results():
+    # the autotuner times one query per task granularity and keeps the fastest; the answer
+    # does not depend on the choice
+    g = synth.chung_lu_planted(20000, 20.0, 2.1, 10, 8, 16, seed=3)
+    G = load(g)
+    ref = [(r[0], r[1]) for r in nuri.topk_cliques(G, 40)]
+    chosen, ms = nuri.tune_cliques(G, 40)
+    assert chosen in (48, 96, 128, 192) and ms > 0
+    assert [(r[0], r[1]) for r in nuri.topk_cliques(G, 40)] == ref
+
+
 def test_edge_cases():
     # empty graph, isolated vertices, self-loops and duplicate pairs
     G = nuri.load_graph(0, np.zeros(0, np.int32), np.zeros(0, np.int32))
