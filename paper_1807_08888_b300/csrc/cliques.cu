@@ -62,6 +62,7 @@ struct QState {
   int64_t defer_count;   // parents sent back because the staging array was full
   int64_t wide_count;    // records handed to the 8-word bitmap tail
   int64_t mid_count;     // records handed to the 4-word bitmap tail
+  int64_t small_count;   // records handed to the 2-word bitmap tail
   int64_t work_next;     // dynamic work counter
   unsigned long long expansions, pruned, dequeued, adj_bytes;
   unsigned long long tail_words;  // adjacency-row words combined by the task kernel
@@ -132,7 +133,8 @@ struct Ctx {
   int64_t stage_cap;
   Rec* deferred;
   Rec* wide;            // records for the 8-word bitmap tail (256 < |P| <= 512)
-  Rec* mid;             // records for the 4-word bitmap tail (64 < |P| <= 256)
+  Rec* mid;             // records for the 4-word bitmap tail (128 < |P| <= 256)
+  Rec* small;           // records for the 2-word bitmap tail (64 < |P| <= 128)
   int32_t* pscratch;    // per-warp global P buffer (max_out entries each)
   int64_t pscratch_stride;
   int32_t k;
@@ -748,10 +750,11 @@ __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
     const int lim = BMW < cx.split_above ? BMW : cx.split_above;  // bitmap tail limit here
     if (W == 1 && p > lim && p <= 64 * KWIDE && p <= cx.split_above) {
       if (lane == 0) {
-        const bool mid = p <= 256;
-        int64_t ds = (int64_t)atomicAdd(
-            (unsigned long long*)(mid ? &cx.st->mid_count : &cx.st->wide_count), 1ull);
-        Rec* r = (mid ? cx.mid : cx.wide) + ds;
+        const int tier = p <= 128 ? 2 : (p <= 256 ? 1 : 0);  // 2, 4 or 8 words a row
+        int64_t* cnt = tier == 2 ? &cx.st->small_count
+                                 : (tier == 1 ? &cx.st->mid_count : &cx.st->wide_count);
+        int64_t ds = (int64_t)atomicAdd((unsigned long long*)cnt, 1ull);
+        Rec* r = (tier == 2 ? cx.small : (tier == 1 ? cx.mid : cx.wide)) + ds;
         r->nv = nv;
         r->bound = bound;
         for (int i = 0; i < nv; ++i) r->V[i] = sV[w][i];
@@ -1479,8 +1482,9 @@ inline int grid_for(int64_t n) {
 
 // Device buffers of the dense-record search: one store per mask width and two task queues.
 struct DenseBufs {
-  DBuf<unsigned long long> rows4, rows8;
-  DBuf<int32_t> vmap4, vmap8, recV4, recV8, recN4, recN8, recP4, recP8;
+  DBuf<unsigned long long> rows2, rows4, rows8;
+  DBuf<int32_t> vmap2, vmap4, vmap8, recV2, recV4, recV8, recN2, recN4, recN8, recP2, recP4,
+      recP8;
   DBuf<unsigned long long> counters;  // [0] slots, [1] queue count, [2] next task
   DBuf<WTask> qa, qb;
   int64_t qcap = 0;
@@ -1489,11 +1493,11 @@ struct DenseBufs {
 
 WideStore make_store(DenseBufs& B, int W, int64_t nrec, cudaStream_t s) {
   const int64_t bmw = 64 * W;
-  DBuf<unsigned long long>& rows = W == 4 ? B.rows4 : B.rows8;
-  DBuf<int32_t>& vmap = W == 4 ? B.vmap4 : B.vmap8;
-  DBuf<int32_t>& recV = W == 4 ? B.recV4 : B.recV8;
-  DBuf<int32_t>& recN = W == 4 ? B.recN4 : B.recN8;
-  DBuf<int32_t>& recP = W == 4 ? B.recP4 : B.recP8;
+  DBuf<unsigned long long>& rows = W == 2 ? B.rows2 : (W == 4 ? B.rows4 : B.rows8);
+  DBuf<int32_t>& vmap = W == 2 ? B.vmap2 : (W == 4 ? B.vmap4 : B.vmap8);
+  DBuf<int32_t>& recV = W == 2 ? B.recV2 : (W == 4 ? B.recV4 : B.recV8);
+  DBuf<int32_t>& recN = W == 2 ? B.recN2 : (W == 4 ? B.recN4 : B.recN8);
+  DBuf<int32_t>& recP = W == 2 ? B.recP2 : (W == 4 ? B.recP4 : B.recP8);
   if ((int64_t)recN.n < nrec) {
     int64_t cap = std::max<int64_t>(nrec, 256);
     rows.alloc(cap * bmw * W, s);
@@ -1687,9 +1691,11 @@ int64_t run_dense(Ctx cx, const Rec* recs, int64_t nrec, int grid, size_t dyn, D
 // Narrow expansion over the batch, then the dense records it handed on (by mask width).
 // ev0/ev1 bracket the CSR expansion launch alone; the task waves are timed in `tt`.
 int64_t launch_expand(Ctx cx, const Rec* in, const int32_t* seeds, int64_t nin, int grid,
-                      DBuf<Rec>& wide, DBuf<Rec>& mid, DenseBufs& B, TailTime& tt,
-                      ResultStore& rs, cudaEvent_t ev0, cudaEvent_t ev1, cudaStream_t s) {
+                      DBuf<Rec>& wide, DBuf<Rec>& mid, DBuf<Rec>& small, DenseBufs& B,
+                      TailTime& tt, ResultStore& rs, cudaEvent_t ev0, cudaEvent_t ev1,
+                      cudaStream_t s) {
   const size_t dyn1 = sizeof(unsigned long long) * KCfg<1>::WARPS * 64;
+  const size_t dyn2 = sizeof(unsigned long long) * KCfg<2>::WARPS * 64 * 2 * 2;
   const size_t dyn4 = sizeof(unsigned long long) * KCfg<4>::WARPS * 64 * 4 * 4;
   const size_t dynw = sizeof(unsigned long long) * KCfg<KWIDE>::WARPS * 64 * KWIDE * KWIDE;
   static const cudaError_t attr = cudaFuncSetAttribute(  // once per process (thread-safe init)
@@ -1700,16 +1706,21 @@ int64_t launch_expand(Ctx cx, const Rec* in, const int32_t* seeds, int64_t nin, 
   NURI_CUDA(attr4);
   cx.wide = wide.p;
   cx.mid = mid.p;
+  cx.small = small.p;
   NURI_CUDA(cudaEventRecord(ev0, s));
   WideStore none;
   memset(&none, 0, sizeof(none));
   k_clique_expand<1><<<grid, KCfg<1>::WARPS * 32, dyn1, s>>>(cx, in, seeds, nin, none);
   NURI_CUDA(cudaGetLastError());
   NURI_CUDA(cudaEventRecord(ev1, s));
-  int64_t counts[2] = {0, 0};  // wide_count, mid_count (adjacent fields)
-  NURI_CUDA(cudaMemcpyAsync(counts, &cx.st->wide_count, 16, cudaMemcpyDeviceToHost, s));
+  int64_t counts[3] = {0, 0, 0};  // wide_count, mid_count, small_count (adjacent fields)
+  NURI_CUDA(cudaMemcpyAsync(counts, &cx.st->wide_count, 24, cudaMemcpyDeviceToHost, s));
   NURI_CUDA(cudaStreamSynchronize(s));
   int64_t launched = 1;
+  if (counts[2] > 0) {
+    compact_results(cx, rs, s);
+    launched += run_dense<2>(cx, small.p, counts[2], grid, dyn2, B, tt, rs, s);
+  }
   if (counts[1] > 0) {
     compact_results(cx, rs, s);
     launched += run_dense<4>(cx, mid.p, counts[1], grid, dyn4, B, tt, rs, s);
@@ -1755,7 +1766,7 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
   k_set_deadline<<<1, 32, 0, s>>>(deadline.p, time_budget_ns());
   DBuf<int32_t> pscratch;
   if (g.max_out > PSMEM) pscratch.alloc((int64_t)total_warps * g.max_out, s);
-  DBuf<Rec> stage, deferred, inbuf, wide, mid;
+  DBuf<Rec> stage, deferred, inbuf, wide, mid, small;
   DenseBufs dense;
   if (G->clique_split_bits > 0) dense.split_bits = G->clique_split_bits;  // tuned per graph
   TailTime tail;
@@ -1933,7 +1944,7 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
       NURI_CUDA(cudaMemsetAsync(&st.p->work_next, 0, sizeof(int64_t), s));
       NURI_CUDA(cudaMemsetAsync(&st.p->stage_count, 0, sizeof(int64_t), s));
       NURI_CUDA(cudaMemsetAsync(&st.p->defer_count, 0, sizeof(int64_t), s));
-      NURI_CUDA(cudaMemsetAsync(&st.p->wide_count, 0, 2 * sizeof(int64_t), s));
+      NURI_CUDA(cudaMemsetAsync(&st.p->wide_count, 0, 3 * sizeof(int64_t), s));
       int64_t nin = 0;
       int src_bucket = -1;
       if (b_front >= b_seed) {
@@ -1960,8 +1971,9 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
         if ((int64_t)deferred.n < nin) deferred.alloc(std::max<int64_t>(nin, 4096), s);
         if ((int64_t)wide.n < nin) wide.alloc(std::max<int64_t>(nin, 4096), s);
         if ((int64_t)mid.n < nin) mid.alloc(std::max<int64_t>(nin, 4096), s);
+        if ((int64_t)small.n < nin) small.alloc(std::max<int64_t>(nin, 4096), s);
         cx.deferred = deferred.p;
-        launches += launch_expand(cx, inbuf.p, nullptr, nin, grid, wide, mid, dense, tail, rs, ev0,
+        launches += launch_expand(cx, inbuf.p, nullptr, nin, grid, wide, mid, small, dense, tail, rs, ev0,
                                   ev1, s);
         cx.res = rs.buf.p;
         cx.res_cap = rs.cap;
@@ -1980,8 +1992,9 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
         if ((int64_t)deferred.n < nin) deferred.alloc(std::max<int64_t>(nin, 4096), s);
         if ((int64_t)wide.n < nin) wide.alloc(std::max<int64_t>(nin, 4096), s);
         if ((int64_t)mid.n < nin) mid.alloc(std::max<int64_t>(nin, 4096), s);
+        if ((int64_t)small.n < nin) small.alloc(std::max<int64_t>(nin, 4096), s);
         cx.deferred = deferred.p;
-        launches += launch_expand(cx, nullptr, svals2.p + lo, nin, grid, wide, mid, dense, tail, rs,
+        launches += launch_expand(cx, nullptr, svals2.p + lo, nin, grid, wide, mid, small, dense, tail, rs,
                                   ev0, ev1, s);
         cx.res = rs.buf.p;
         cx.res_cap = rs.cap;
