@@ -533,6 +533,10 @@ __device__ void dense_node(const Ctx& cx, const WideStore& ws, int slot, int dep
         limit_hit = true;
         level_ok = false;
       }
+      if (level_ok && !cx.no_prune && size + popc<W>(R, wa) < t_cache) {  // |V| + |P| < tau
+        ++my_pruned;
+        level_ok = false;
+      }
       if (level_ok && !cx.no_prune && size < t_cache) {
         const int kmin = t_cache - size;  // classes 1 .. kmin-1 cannot reach tau
         for (int c = 1; c < kmin && any<W>(R, wa); ++c) {
@@ -1144,6 +1148,10 @@ __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
             level_ok = any<W>(R, wa);
             if (level_ok && size >= MAXD) {
               limit_hit = true;
+              level_ok = false;
+            }
+            if (level_ok && !cx.no_prune && size + popc<W>(R, wa) < t_cache) {
+              ++my_pruned;  // |V| + |P| < tau: no colouring needed
               level_ok = false;
             }
             if (level_ok && !cx.no_prune && size < t_cache) {
