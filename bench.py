@@ -106,6 +106,20 @@ class Clocks:
                 "samples": len(self.rows)}
 
 
+def combine_ranks(total_ms, total_units, dist=None, device="cpu"):
+    """Whole-job aggregate over replicas: the slowest rank's time and the units of all ranks
+    (value = units / time).  Works with any torch.distributed backend (gloo on CPU in tests,
+    NCCL on the GPUs)."""
+    if dist is None:
+        return float(total_ms), float(total_units)
+    import torch
+    tm = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    tu = torch.tensor([float(total_units)], dtype=torch.float64, device=device)
+    dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tu, op=dist.ReduceOp.SUM)
+    return float(tm.item()), float(tu.item())
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -240,11 +254,7 @@ def main():
     total_ms = float(sum(times))
     total_exp = float(sum(exps))
     if dist:
-        t = torch.tensor([total_ms, total_exp], dtype=torch.float64, device="cuda")
-        tm = t.clone()
-        dist.all_reduce(tm[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        total_ms, total_exp = float(tm[0]), float(t[1])
+        total_ms, total_exp = combine_ranks(total_ms, total_exp, dist, device="cuda")
     value = total_exp / (total_ms / 1e3)
     peak, peak_kind = peaks()
     # CSR expansion (k_clique_expand over frontier records and seeds): adjacency bytes over
