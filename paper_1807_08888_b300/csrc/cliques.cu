@@ -353,6 +353,14 @@ struct WideStore {
   int32_t split_bits;
   const unsigned long long* in_next;  // fetch counter of the wave's input (tasks kernel)
   int64_t in_n;                       // tasks in the wave's input
+  // tie-aware pruning (all-cliques ranking): at least k known results rank before every
+  // clique of size lex_tau whose smallest vertex id exceeds lex_first.  low (per slot, W
+  // words) marks the candidates with id <= lex_first, reclow the slots whose record holds
+  // such a vertex.  lex_tau = INT32_MIN: off.
+  const unsigned long long* low;
+  const int32_t* reclow;
+  int32_t lex_tau;
+  int32_t lex_first;
 };
 
 // Visit the node (record + picks[0..depth], candidates Pn, explored Xn) of a dense record and
@@ -488,6 +496,15 @@ __device__ void dense_node(const Ctx& cx, const WideStore& ws, int slot, int dep
   const int base_depth = depth;
   int local = 0;      // nodes entered by this call
   bool fresh = true;  // the node at `depth` (candidates Pn) has not been coloured yet
+  // lowc[d]: the clique at depth d holds a vertex with id <= lex_first (tie-aware pruning)
+  const bool lex = ws.lex_tau != INT32_MIN;
+  const unsigned long long* lowm = lex ? ws.low + (int64_t)slot * W : nullptr;
+  uint8_t lowc[MAXD + 1];
+  if (lex) {
+    bool lc = ws.reclow[slot] != 0;
+    for (int q = 0; q <= depth && !lc; ++q) lc = (lowm[pick[q] >> 6] >> (pick[q] & 63)) & 1ull;
+    lowc[depth] = lc ? 1 : 0;
+  }
   while (!out_of_time) {
     bool level_ok = true;
     if (fresh) {
@@ -550,6 +567,29 @@ __device__ void dense_node(const Ctx& cx, const WideStore& ws, int slot, int dep
           level_ok = false;
         }
       }
+      // tie-aware pruning: no clique below this node can exceed tau (one more colour class
+      // empties R) and every clique below it would have its smallest id above lex_first
+      // (neither the clique nor any candidate holds a smaller one): at least k known results
+      // rank before each of them
+      if (level_ok && lex && ws.lex_tau == t_cache && size < t_cache && !lowc[depth]) {
+        unsigned long long hit = 0;
+#pragma unroll
+        for (int q = 0; q < W; ++q)
+          if (q < wa) hit |= Pn[q] & lowm[q];
+        if (!hit) {
+          unsigned long long cls[W], R2[W];
+#pragma unroll
+          for (int q = 0; q < W; ++q) {
+            cls[q] = R[q];
+            R2[q] = R[q];
+          }
+          colour_class<W>(cls, R2, rows, wa, my_words);
+          if (!any<W>(R2, wa)) {
+            ++my_pruned;
+            level_ok = false;
+          }
+        }
+      }
       if (level_ok) {
         // the stack keeps only the record's live words (q < wa); reads mask the rest
 #pragma unroll
@@ -586,6 +626,7 @@ __device__ void dense_node(const Ctx& cx, const WideStore& ws, int slot, int dep
             Xn[q] = q < wa ? (stkX[depth][q] & rows[u * W + q]) : 0ull;
           stkX[depth][qu] |= ubit;
         }
+        if (lex) lowc[depth + 1] = lowc[depth] | (uint8_t)((lowm[u >> 6] >> (u & 63)) & 1ull);
         ++depth;
         pick[depth] = (uint16_t)u;
         visit_node(depth, Pn, Xn);
@@ -1495,6 +1536,11 @@ struct DenseBufs {
       recP8;
   DBuf<unsigned long long> counters;  // [0] slots, [1] queue count, [2] next task
   DBuf<WTask> qa, qb;
+  DBuf<unsigned long long> low2, low4, low8;  // tie-aware pruning masks per slot
+  DBuf<int32_t> reclow2, reclow4, reclow8;
+  DBuf<int32_t> lexbuf;                      // smallest id of each size-tau result
+  DBuf<unsigned long long> lexcnt;
+  bool lex_allowed = false;  // all-cliques ranking, pruning on, ties not kept
   int64_t qcap = 0;
   int32_t split_bits = 96;  // nodes with more candidates become tasks (measured best on B300)
 };
@@ -1506,6 +1552,8 @@ WideStore make_store(DenseBufs& B, int W, int64_t nrec, cudaStream_t s) {
   DBuf<int32_t>& recV = W == 2 ? B.recV2 : (W == 4 ? B.recV4 : B.recV8);
   DBuf<int32_t>& recN = W == 2 ? B.recN2 : (W == 4 ? B.recN4 : B.recN8);
   DBuf<int32_t>& recP = W == 2 ? B.recP2 : (W == 4 ? B.recP4 : B.recP8);
+  DBuf<unsigned long long>& low = W == 2 ? B.low2 : (W == 4 ? B.low4 : B.low8);
+  DBuf<int32_t>& reclow = W == 2 ? B.reclow2 : (W == 4 ? B.reclow4 : B.reclow8);
   if ((int64_t)recN.n < nrec) {
     int64_t cap = std::max<int64_t>(nrec, 256);
     rows.alloc(cap * bmw * W, s);
@@ -1513,6 +1561,10 @@ WideStore make_store(DenseBufs& B, int W, int64_t nrec, cudaStream_t s) {
     recV.alloc(cap * MAXD, s);
     recN.alloc(cap, s);
     recP.alloc(cap, s);
+    if (B.lex_allowed) {
+      low.alloc(cap * W, s);
+      reclow.alloc(cap, s);
+    }
   }
   if (!B.counters.p) B.counters.alloc(3, s);
   if (!B.qa.p) {
@@ -1534,6 +1586,10 @@ WideStore make_store(DenseBufs& B, int W, int64_t nrec, cudaStream_t s) {
   ws.q_count = B.counters.p + 1;
   ws.q_cap = B.qcap;
   ws.split_bits = B.split_bits;
+  ws.low = low.p;
+  ws.reclow = reclow.p;
+  ws.lex_tau = INT32_MIN;
+  ws.lex_first = 0;
   return ws;
 }
 
@@ -1609,6 +1665,49 @@ void compact_results(Ctx& cx, ResultStore& rs, cudaStream_t s) {
   cx.res_cap = rs.cap;
 }
 
+// Smallest original vertex id of every stored result of size tau (tie-aware pruning).
+__global__ void k_row_minid(const Rec* __restrict__ res, int64_t n, int32_t tau,
+                            const int32_t* __restrict__ vert_of, int32_t* __restrict__ out,
+                            unsigned long long* __restrict__ cnt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < n; i += nwarps) {
+    const int nv = res[i].nv;
+    if (nv != tau) continue;
+    int32_t m = INT32_MAX;
+    for (int a = lane; a < nv; a += 32) m = min(m, __ldg(vert_of + res[i].V[a]));
+    for (int o = 16; o; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) out[atomicAdd(cnt, 1ull)] = m;
+  }
+}
+
+// Per store slot: the candidates with vertex id <= first (mask of W words) and whether the
+// record itself holds such a vertex.  One warp per slot.
+template <int W>
+__global__ void k_lex_low(WideStore ws, int64_t nslots, const int32_t* __restrict__ vert_of,
+                          int32_t first, unsigned long long* __restrict__ low,
+                          int32_t* __restrict__ reclow) {
+  constexpr int BMW = 64 * W;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t sl = warp; sl < nslots; sl += nwarps) {
+    if (lane < W) low[sl * W + lane] = 0ull;
+    __syncwarp();
+    const int p = ws.recP[sl];
+    for (int a = lane; a < p; a += 32)
+      if (__ldg(vert_of + ws.vmap[sl * BMW + a]) <= first)
+        atomicOr(&low[sl * W + (a >> 6)], 1ull << (a & 63));
+    const int nv = ws.recN[sl];
+    bool any_low = false;
+    for (int a = lane; a < nv; a += 32) any_low |= __ldg(vert_of + ws.recV[sl * MAXD + a]) <= first;
+    any_low = __any_sync(0xffffffffu, any_low);
+    if (lane == 0) reclow[sl] = any_low ? 1 : 0;
+    __syncwarp();
+  }
+}
+
 // Device time and launches of the task kernel (CUDA events around every wave).
 struct TailTime {
   double ms = 0.0;
@@ -1623,6 +1722,60 @@ struct TailTime {
     cudaEventDestroy(b);
   }
 };
+
+// Tie-aware pruning threshold for the next wave: with c_hi known results larger than tau and
+// at least need = k - c_hi stored results of size tau, lex_first = the need-th smallest of
+// their smallest ids; every clique of size tau whose smallest id exceeds it ranks after k
+// known results.  Off (lex_tau = INT32_MIN) when there are not enough such results yet.
+template <int W>
+void update_lex(const Ctx& cx, WideStore& ws, ResultStore& rs, DenseBufs& B, cudaStream_t s) {
+  int32_t tau = 0;
+  int64_t rc = 0;
+  std::vector<int32_t> hist(MAXD + 2, 0);
+  NURI_CUDA(cudaMemcpyAsync(&tau, &cx.st->tau, 4, cudaMemcpyDeviceToHost, s));
+  NURI_CUDA(cudaMemcpyAsync(&rc, &cx.st->res_count, 8, cudaMemcpyDeviceToHost, s));
+  NURI_CUDA(cudaMemcpyAsync(hist.data(), cx.st->hist, sizeof(int32_t) * (MAXD + 2),
+                            cudaMemcpyDeviceToHost, s));
+  NURI_CUDA(cudaStreamSynchronize(s));
+  int64_t c_hi = 0;
+  for (int c = std::max(tau + 1, 0); c <= MAXD + 1; ++c) c_hi += hist[c];
+  const int64_t need = (int64_t)cx.k - c_hi;
+  if (tau < 1 || tau > MAXD || need <= 0 || rc > rs.cap || rc <= 0) {
+    ws.lex_tau = INT32_MIN;
+    return;
+  }
+  if ((int64_t)B.lexbuf.n < rc) B.lexbuf.alloc(std::max<int64_t>(rc, 4096), s);
+  if (!B.lexcnt.p) B.lexcnt.alloc(1, s);
+  NURI_CUDA(cudaMemsetAsync(B.lexcnt.p, 0, 8, s));
+  k_row_minid<<<std::max(1, std::min<int>((int)((rc + 7) / 8), sm_count() * 16)), 256, 0, s>>>(
+      rs.buf.p, rc, tau, cx.g.vert_of, B.lexbuf.p, B.lexcnt.p);
+  NURI_CUDA(cudaGetLastError());
+  unsigned long long m = 0;
+  NURI_CUDA(cudaMemcpyAsync(&m, B.lexcnt.p, 8, cudaMemcpyDeviceToHost, s));
+  NURI_CUDA(cudaStreamSynchronize(s));
+  if ((int64_t)m < need) {
+    ws.lex_tau = INT32_MIN;
+    return;
+  }
+  std::vector<int32_t> ids(m);
+  NURI_CUDA(cudaMemcpyAsync(ids.data(), B.lexbuf.p, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, s));
+  NURI_CUDA(cudaStreamSynchronize(s));
+  std::nth_element(ids.begin(), ids.begin() + (need - 1), ids.end());
+  const int32_t first = ids[need - 1];
+  if (ws.lex_tau == tau && ws.lex_first == first) return;  // masks still valid
+  unsigned long long nslots = 0;
+  NURI_CUDA(cudaMemcpyAsync(&nslots, B.counters.p, 8, cudaMemcpyDeviceToHost, s));
+  NURI_CUDA(cudaStreamSynchronize(s));
+  nslots = std::min<unsigned long long>(nslots, (unsigned long long)ws.slot_cap);
+  if (nslots > 0) {
+    k_lex_low<W><<<std::max(1, std::min<int>((int)((nslots + 7) / 8), sm_count() * 16)), 256, 0,
+                   s>>>(ws, (int64_t)nslots, cx.g.vert_of, first,
+                        const_cast<unsigned long long*>(ws.low), const_cast<int32_t*>(ws.reclow));
+    NURI_CUDA(cudaGetLastError());
+  }
+  ws.lex_tau = tau;
+  ws.lex_first = first;
+}
 
 // Dense records of one width: the warp kernel stores them and queues their children, then
 // task waves run until the queue is empty.  A wave's grid is the resident capacity of the
@@ -1663,6 +1816,7 @@ int64_t run_dense(Ctx cx, const Rec* recs, int64_t nrec, int grid, size_t dyn, D
     int64_t n = std::min<int64_t>((int64_t)cnt, B.qcap);
     if (n == 0) break;
     compact_results(cx, rs, s);
+    if (B.lex_allowed) update_lex<W>(cx, ws, rs, B, s);
     int32_t err = 0;
     NURI_CUDA(cudaMemcpyAsync(&err, &cx.st->err, 4, cudaMemcpyDeviceToHost, s));
     NURI_CUDA(cudaStreamSynchronize(s));
@@ -1777,6 +1931,8 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
   DBuf<Rec> stage, deferred, inbuf, wide, mid, small;
   DenseBufs dense;
   if (G->clique_split_bits > 0) dense.split_bits = G->clique_split_bits;  // tuned per graph
+  // tie-aware pruning: all-cliques ranking with pruning, exactly k rows (NURI_NO_LEX: off)
+  dense.lex_allowed = !maximal && !no_prune && !keep_ties && getenv("NURI_NO_LEX") == nullptr;
   TailTime tail;
   stage.alloc(stage_cap, s);
   ++launches;

@@ -191,6 +191,18 @@ def test_result_compaction_keeps_the_top_k(monkeypatch):
     assert [(r[0], r[1]) for r in got] == [(r[0], r[1]) for r in ref]
 
 
+def test_tie_aware_pruning_keeps_results(monkeypatch):
+    # the lexicographic threshold (smallest id of the k-th result among ties) prunes only
+    # cliques that rank after k known results: same rows with it switched off
+    g = synth.chung_lu_planted(20000, 20.0, 2.1, 10, 8, 16, seed=5)
+    G = load(g)
+    on = [(r[0], r[1]) for r in nuri.topk_cliques(G, 60)]
+    monkeypatch.setenv("NURI_NO_LEX", "1")
+    off = [(r[0], r[1]) for r in nuri.topk_cliques(G, 60)]
+    monkeypatch.delenv("NURI_NO_LEX")
+    assert on == off
+
+
 def test_tune_cliques_keeps_results():
     # the autotuner times one query per task granularity and keeps the fastest; the answer
     # does not depend on the choice
