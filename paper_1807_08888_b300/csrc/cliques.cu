@@ -47,6 +47,8 @@ constexpr int MAXD = 256;      // largest clique the records can hold
 constexpr int NB = 1024;       // frontier buckets by bound (bucket NB-1 holds every bound
                                // >= NB-1; cliques never exceed MAXD < NB-1)
 constexpr int PSMEM = 512;     // P entries staged in shared memory per warp
+constexpr int CB_ROWS = 1024;  // candidates the split tier's colouring check handles
+constexpr int CB_W = CB_ROWS / 64;
 
 struct Rec {
   int32_t nv;
@@ -136,6 +138,8 @@ struct Ctx {
   Rec* mid;             // records for the 4-word bitmap tail (128 < |P| <= 256)
   Rec* small;           // records for the 2-word bitmap tail (64 < |P| <= 128)
   int32_t* pscratch;    // per-warp global P buffer (max_out entries each)
+  unsigned long long* cbits;  // per-warp adjacency bitmap (CB_ROWS x CB_W words) for the
+                              // colouring check of split records; null when unused
   int64_t pscratch_stride;
   int32_t k;
   int32_t maximal;
@@ -806,6 +810,59 @@ __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
         --my_deq;
       }
       continue;
+    }
+    // a record too wide for the bitmap tiers (512 < |P| <= 1024) is first coloured greedily on
+    // an adjacency bitmap of P (global scratch): if the colours do not lift it to tau, no
+    // clique below it can, and it is dropped before its children are created
+    if (W == 1 && cx.cbits && !cx.no_prune && p > 64 * KWIDE && p <= CB_ROWS && nv < tau) {
+      unsigned long long* cb = cx.cbits + gwarp * (int64_t)CB_ROWS * CB_W;
+      const int cw = (p + 63) >> 6;
+      for (int64_t i = lane; i < (int64_t)p * CB_W; i += 32) cb[i] = 0ull;
+      __syncwarp();
+      const int32_t plast = P[p - 1];
+      for (int i = 0; i < p; ++i) {
+        const int32_t pi = P[i];
+        const int64_t rb = g.ooff[pi], re = g.ooff[pi + 1];
+        for (int64_t t = rb + lane; t < re; t += 32) {
+          const int32_t x = __ldg(g.oout + t);
+          if (x > plast) continue;
+          const int j = lower_bound_dev(P, i + 1, p, x);  // out-neighbours rank above pi
+          if (j < p && P[j] == x) {
+            atomicOr(&cb[(int64_t)i * CB_W + (j >> 6)], 1ull << (j & 63));
+            atomicOr(&cb[(int64_t)j * CB_W + (i >> 6)], 1ull << (i & 63));
+          }
+        }
+      }
+      __syncwarp();
+      int drop = 0;
+      if (lane == 0) {
+        unsigned long long left[CB_W], cls[CB_W];
+        for (int q = 0; q < CB_W; ++q)
+          left[q] = q < cw ? ((q == cw - 1 && (p & 63)) ? ((1ull << (p & 63)) - 1) : ~0ull) : 0ull;
+        const int need = tau - nv;  // colours the record needs to reach tau
+        int colours = 0;
+        bool rest = true;
+        while (rest && colours < need) {
+          ++colours;
+          for (int q = 0; q < CB_W; ++q) cls[q] = left[q];
+          for (int q = 0; q < cw; ++q)
+            while (cls[q]) {
+              const int b = __ffsll((long long)cls[q]) - 1;
+              const unsigned long long bit = 1ull << b;
+              cls[q] &= ~bit;
+              left[q] &= ~bit;
+              const unsigned long long* row = cb + (int64_t)(q * 64 + b) * CB_W;
+              for (int r = q; r < cw; ++r) cls[r] &= ~row[r];
+            }
+          unsigned long long a = 0;
+          for (int q = 0; q < cw; ++q) a |= left[q];
+          rest = a != 0;
+        }
+        drop = (!rest && colours < need) ? 1 : 0;  // |V| + colours < tau
+        if (drop) ++my_pruned;
+      }
+      drop = __shfl_sync(FULL, drop, 0);
+      if (drop) continue;
     }
     // a record that must be split reserves its children's staging slots first; if the
     // staging array is full it goes back to the frontier untouched (re-dequeued later)
@@ -1928,6 +1985,9 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
   k_set_deadline<<<1, 32, 0, s>>>(deadline.p, time_budget_ns());
   DBuf<int32_t> pscratch;
   if (g.max_out > PSMEM) pscratch.alloc((int64_t)total_warps * g.max_out, s);
+  DBuf<unsigned long long> cbits;  // colouring check of split records (512 < |P| <= 1024)
+  if (g.max_out > 64 * KWIDE && !no_prune)
+    cbits.alloc((int64_t)total_warps * CB_ROWS * CB_W, s);
   DBuf<Rec> stage, deferred, inbuf, wide, mid, small;
   DenseBufs dense;
   if (G->clique_split_bits > 0) dense.split_bits = G->clique_split_bits;  // tuned per graph
@@ -2056,6 +2116,7 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
     cx.stage_cap = stage_cap;
     cx.pscratch = pscratch.p;
     cx.pscratch_stride = g.max_out;
+    cx.cbits = cbits.p;
     cx.k = k;
     cx.maximal = maximal;
     cx.no_prune = no_prune;
@@ -2127,11 +2188,24 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
           hb.count = hn;
           stats.reloaded += hn;
         }
-        nin = std::min<int64_t>(hb.count, std::max<int64_t>(total_warps * 2, 4096));
-        if ((int64_t)inbuf.n < nin) inbuf.alloc(std::max<int64_t>(nin, 4096), s);
+        const int64_t target = std::max<int64_t>(total_warps * 2, 4096);
+        nin = std::min<int64_t>(hb.count, target);
+        if ((int64_t)inbuf.n < target) inbuf.alloc(target, s);
         NURI_CUDA(cudaMemcpyAsync(inbuf.p, hb.dev.p + (hb.count - nin), sizeof(Rec) * nin,
                                   cudaMemcpyDeviceToDevice, s));
         hb.count -= nin;
+        // a thin bucket does not fill a launch: take more records from the next buckets down
+        // (still above tau and above the best pending seed); the order only changes the work
+        for (int b2 = b_front - 1; b2 >= 0 && nin < target; --b2) {
+          if (b2 < b_seed || (!no_prune && b2 < tau && b2 != NB - 1)) break;
+          HostBucket& h2 = buckets[b2];
+          if (h2.count == 0) continue;
+          const int64_t take = std::min<int64_t>(h2.count, target - nin);
+          NURI_CUDA(cudaMemcpyAsync(inbuf.p + nin, h2.dev.p + (h2.count - take),
+                                    sizeof(Rec) * take, cudaMemcpyDeviceToDevice, s));
+          h2.count -= take;
+          nin += take;
+        }
         if ((int64_t)deferred.n < nin) deferred.alloc(std::max<int64_t>(nin, 4096), s);
         if ((int64_t)wide.n < nin) wide.alloc(std::max<int64_t>(nin, 4096), s);
         if ((int64_t)mid.n < nin) mid.alloc(std::max<int64_t>(nin, 4096), s);
