@@ -3,31 +3,39 @@
 //
 //   P_s        = common neighbours of the members that come after every member in the
 //                canonical order (Listing 1's set with the canonical extension of Section 3.2);
-//                here the order is the degree orientation rank (any total order enumerates
+//                here the order is a degeneracy (core-peeling) rank (any total order enumerates
 //                every clique exactly once; results are reported in original ids)
 //   expandable = d in P_s;  relevant = true (all cliques) or maximality (flag)
-//   bound      = |V_s| + |P_s| (Carraghan-Pardalos), tightened inside the bitmap tail to
+//   bound      = |V_s| + |P_s| (Carraghan-Pardalos), tightened on adjacency bitmaps to
 //                |V_s| + (colours of a greedy colouring of P_s); prune iff bound < tau (strict)
-//   tau        = k-th best size among results found so far (global, atomicMax, monotone)
+//   tau        = k-th best size among results found so far (global, atomicMax, monotone); in
+//                the all-cliques ranking also lifted by subset counts (a c-clique holds
+//                C(c, s) s-cliques) and by a greedy warm start before the search
 //
 // Work is organised as a bucketed best-first frontier driven from the host:
 //   * seeds (one per vertex, Algorithm 1's initialisation) are sorted by bound and consumed in
-//     descending-bound chunks; frontier records live in 256 buckets keyed by bound (LIFO
-//     inside a bucket, so the deepest records of the best bound go first);
-//   * each round takes the highest bucket (or seed chunk) whose bound >= tau and expands it
-//     with one warp per record (k_clique_expand);
+//     descending-bound chunks (narrow seeds first); frontier records live in 1024 buckets
+//     keyed by bound (LIFO inside a bucket, so the deepest records of the best bound go first);
+//   * each round takes the highest bucket (or seed chunk) whose bound >= tau, topped up from
+//     the next buckets when thin, and expands it with one warp per record (k_clique_expand);
 //   * a record with |P| <= 64 is finished in place: the warp builds the 64x64 bit adjacency
-//     of P in shared memory and its lanes run independent depth-first searches over the
-//     subtrees of the record's children with AND + popc (the bitmap tail);
-//   * a record with |P| > 64 is split: for every d in P the warp intersects the suffix of P
-//     after d with N+(d) (binary search + ballot/popc), and children whose bound >= tau go
-//     to a staging array that is scattered into the buckets;
+//     of P in shared memory and its lanes search the record's subtrees (colour-ordered
+//     branching over lane tasks);
+//   * a record with 64 < |P| <= 512 goes to a dense tier (2, 4 or 8 words a row): its bitmap
+//     is stored once and its search nodes become tasks of a global queue (k_clique_tasks),
+//     coloured once each, with continuation tasks donated from busy lanes and tie-aware
+//     pruning against the k-th tied result;
+//   * a record with |P| > 512 is first coloured on a bitmap when |P| <= 1024 (dropped if the
+//     colours cannot reach tau), else split: for every d in P the warp intersects the suffix
+//     of P after d with N+(d) (binary search + ballot/popc), and children whose bound >= tau
+//     go to a staging array that is scattered into the buckets;
 //   * buckets that overflow the device frontier capacity are spilled to pinned host memory
 //     (the role of the paper's disk-backed virtual priority queue, Section 5) and reloaded,
 //     filtered by tau, when they become the highest bucket.
-// Results (clique records with size >= tau when processed) are appended to a device buffer;
-// a histogram of their sizes drives tau.  A final kernel sequence selects the rows with
-// size >= tau, maps them to original ids, sorts them by (size desc, ids lex asc) and keeps k.
+// Results (clique records with size >= tau when processed) are appended to a device buffer
+// that is compacted in flight; a histogram of their sizes drives tau.  A final kernel sequence
+// selects the rows with size >= tau, maps them to original ids, sorts them by (size desc, ids
+// lex asc) and keeps k.
 #include <cub/cub.cuh>
 
 #include <algorithm>
