@@ -639,7 +639,9 @@ void topk_iso_batch(nuri_graph* G, int32_t nqueries, const nuri_query* qs, const
   // per-query state, histograms, result regions
   std::vector<long long> tau_init(nqueries, -1);
   std::vector<int64_t> cap(nqueries), rbase(nqueries + 1);
-  for (int i = 0; i < nqueries; ++i) cap[i] = std::max<int64_t>(4096, (int64_t)ks[i] * 8);
+  // result rows per query (40 B each): room for the rows recorded while tau is still low, so
+  // that an overflow (which re-runs the batch) stays rare
+  for (int i = 0; i < nqueries; ++i) cap[i] = std::max<int64_t>(16384, (int64_t)ks[i] * 64);
   if (const char* e = getenv("NURI_RESULT_CAP"))
     for (int i = 0; i < nqueries; ++i) cap[i] = std::max<int64_t>(1, atoll(e));
   std::vector<char> active(nqueries, 1);
