@@ -89,6 +89,8 @@ typedef struct nuri_stats {
   double tail_ms;          /* cliques: summed device time of those launches        */
   int64_t tail_words;      /* cliques: 64-bit adjacency-row words the task kernel
                               combined into candidate masks (colouring, branching) */
+  int64_t dense_records[3];/* cliques: records searched on 2-, 4- and 8-word bitmap rows
+                              (65..128, 129..256 and 257..512 candidates)           */
 } nuri_stats;
 
 /* A result set.  Row i has score[i]; its vertices are verts[vert_off[i] .. vert_off[i+1])
@@ -236,6 +238,44 @@ nuri_status nuri_hop_index_noalloc(int32_t n, const int64_t* off, const int32_t*
                                    void* stream);
 
 /*
+ * Seed partition: one query split over several GPUs (or processes), each running the same
+ * query on a copy of the graph with a part of the seeds.  Algorithm 1's seeds are independent
+ * units (Section 3.2: every subgraph grows from one unit subgraph), so the parts share
+ * nothing but the threshold: each part only needs to know that the k-th best score is at
+ * least some value to prune with it.
+ *   index, count  this part and the number of parts (count = 1: no partition).  A seed
+ *                 belongs to part nuri_seed_part(v, count), v its original vertex id: for
+ *                 cliques the vertex every clique below the seed starts from (its first
+ *                 vertex in the library's canonical order), for isomorphism the data vertex
+ *                 the query's root is mapped to.
+ *   exchange      called on the host between rounds (cliques: every frontier round;
+ *                 isomorphism: between seed chunks) with the query index in its batch and
+ *                 the part's current threshold (INT64_MIN while it has fewer than k rows);
+ *                 returns the largest threshold any part has published so far (which the
+ *                 part then prunes with).  It must not wait for the other parts: parts run
+ *                 different numbers of rounds.  NULL: no exchange.
+ * A partitioned query returns the part's own top k: every row of the global top k whose
+ * seed lies in the part, with the same ranking; merging the parts' rows by the ranking and
+ * keeping k gives the global answer.  The query's other counters are the part's own.
+ */
+typedef int64_t (*nuri_tau_exchange_fn)(void* ctx, int32_t query, int64_t local_tau);
+typedef struct nuri_partition {
+  int32_t index;
+  int32_t count;
+  nuri_tau_exchange_fn exchange;
+  void* ctx;
+} nuri_partition;
+
+/* Set (or, with p = NULL or p->count == 1, clear) the seed partition of every later clique
+ * and isomorphism query on g.  Errors: NURI_ERR_INVALID (count < 1, index outside
+ * 0..count-1). */
+nuri_status nuri_set_partition(nuri_graph* g, const nuri_partition* p);
+
+/* The part a seed vertex id belongs to among `count` parts: a fixed integer mix of v (the
+ * 32-bit finaliser of MurmurHash3) modulo count.  Host function; needs no GPU. */
+int32_t nuri_seed_part(int32_t v, int32_t count);
+
+/*
  * nuri_tune_cliques -- autotune the dense-record search of top-k clique queries on this graph
  * (the batched form's work granularity; no counterpart in the paper, whose search is
  * sequential).  Runs the query (g, k, flags) once per candidate task granularity (48, 96,
@@ -263,32 +303,61 @@ void nuri_free_result(nuri_result* r);
 
 #define NURI_REQ_CLIQUES 0
 #define NURI_REQ_ISO 1
+#define NURI_REQ_PATTERNS 2
 
-/* One request: kind NURI_REQ_CLIQUES (rank NURI_RANK_SIZE, flags as nuri_topk_cliques) or
- * NURI_REQ_ISO (query, rank WEIGHT_SUM or DEGREE_SUM, flags as nuri_topk_iso).  The query
- * arrays are copied at submission. */
+/* One request: kind NURI_REQ_CLIQUES (rank NURI_RANK_SIZE, flags as nuri_topk_cliques),
+ * NURI_REQ_ISO (query, rank WEIGHT_SUM or DEGREE_SUM, flags as nuri_topk_iso) or
+ * NURI_REQ_PATTERNS (pattern_edges = M in 1..5, rank NURI_RANK_MNI; nuri_topk_batch only).
+ * The query arrays are copied at submission. */
 typedef struct nuri_request {
   int32_t kind;
   int32_t k;
   int32_t rank;
   uint32_t flags;
   nuri_query query;
+  int32_t pattern_edges;
+  int32_t pad;
 } nuri_request;
+
+/*
+ * nuri_topk_batch -- many top-k requests of any kind on one graph in one call (Algorithm 1 /
+ * Algorithm 2 run per query, Section 3; the batched form of the engine).  outs[i] receives
+ * request i's result, exactly what the request alone returns (rows; the counters in `stats`
+ * are those of the shared work that produced it).  How requests share work:
+ *   - cliques with equal flags: the ranking (size desc, sorted ids asc) does not depend on
+ *     k, so every request's rows are a prefix of the top-K list, K = the largest k of the
+ *     group; one search with K answers them all (with NURI_KEEP_TIES: one search keeping
+ *     ties, each request keeping the rows that tie with its own k-th);
+ *   - patterns with equal M and flags: the same, one Algorithm 2 run per M;
+ *   - isomorphism requests with equal rank and flags: one batched launch, as
+ *     nuri_topk_iso_batch (every query keeps its own frontier and threshold).
+ * Errors: NURI_ERR_INVALID (a bad request: unknown kind, k < 1, bad query, M outside 1..5),
+ * or the first error of a query run; on any error every outs[i] is NULL.
+ */
+nuri_status nuri_topk_batch(nuri_graph* g, int32_t nreq, const nuri_request* reqs,
+                            void* stream, nuri_result** outs);
 
 /* slots: concurrent requests (one CUDA stream and one host worker each, default 4);
  * max_batch: isomorphism requests merged into one launch (default 64);
- * mem_budget_bytes: device memory admitted requests may hold together (default 8 GiB). */
+ * mem_budget_bytes: device memory admitted requests may hold together, plus the clique
+ * kernels' local memory that the driver reserves once per context (0: 80 % of the device
+ * memory free when the server is created). */
 typedef struct nuri_server_cfg {
   int32_t slots;
   int32_t max_batch;
   int64_t mem_budget_bytes;
 } nuri_server_cfg;
 
-/* Host-clock times of a finished request: waiting for admission, running, and both. */
+/* Host-clock times of a finished request: waiting for admission, running, and both; the
+ * start and end of its service on the host's monotonic clock (milliseconds, any origin;
+ * comparable between requests of one process); and the device bytes it was admitted with. */
 typedef struct nuri_request_times {
   double queue_ms;
   double service_ms;
   double total_ms;
+  double start_ms;
+  double done_ms;
+  int64_t mem_bytes;
 } nuri_request_times;
 
 typedef struct nuri_server nuri_server;
@@ -296,9 +365,9 @@ typedef struct nuri_server nuri_server;
 /*
  * nuri_server_create -- start a request server on a loaded graph (the graph must outlive it).
  * Requests are admitted oldest first as soon as a slot is free and their device-memory
- * estimate fits the budget; isomorphism requests waiting together run as one batched launch
- * (the frontier-level batching of nuri_topk_iso_batch).  Results are identical to the same
- * query run alone.
+ * estimate (nuri_request_bytes) fits the budget; requests waiting together run as one
+ * nuri_topk_batch call: isomorphism requests as one batched launch, clique requests with the
+ * same flags as one shared search.  Results are identical to the same query run alone.
  */
 nuri_status nuri_server_create(nuri_graph* g, const nuri_server_cfg* cfg, nuri_server** out);
 /* Queue a request (thread-safe); *ticket identifies it. */
@@ -313,6 +382,23 @@ nuri_status nuri_server_wait(nuri_server* s, uint64_t ticket, nuri_result** out,
                              nuri_request_times* times);
 /* Number of batched isomorphism launches and of requests they carried. */
 nuri_status nuri_server_stats(nuri_server* s, int64_t* batches, int64_t* batched);
+/* Number of shared clique searches and of clique requests they answered. */
+nuri_status nuri_server_clique_stats(nuri_server* s, int64_t* searches, int64_t* requests);
+/* The server's device-memory budget and the part of it held for the whole run (the clique
+ * kernels' local memory, reserved once per context); either pointer may be NULL. */
+nuri_status nuri_server_budget(nuri_server* s, int64_t* budget_bytes, int64_t* fixed_bytes);
+
+/*
+ * nuri_request_bytes -- the device memory a request may hold while it runs: an upper bound of
+ * every buffer its query allocates on graph g (for cliques: seeds, staging, the device
+ * frontier at its default capacity, round arrays, split-tier scratch, dense-record stores
+ * and task queues at their maximum, the initial result set and the final merge; for
+ * isomorphism: seeds, result region, selection and merge).  This is the figure the server
+ * admits requests by.  A clique result set that outgrows its initial size (compaction keeps
+ * it to the rows at or above the threshold first) adds to it.
+ * Errors: NURI_ERR_INVALID (NULL arguments, k < 1, unknown kind).
+ */
+nuri_status nuri_request_bytes(const nuri_graph* g, const nuri_request* r, int64_t* bytes);
 /* Finish every queued request, stop the workers, free unclaimed results. */
 void nuri_server_destroy(nuri_server* s);
 

@@ -20,7 +20,8 @@ import numpy as np
 
 __all__ = [
     "NuriError", "lib", "load_graph", "Graph", "topk_cliques", "topk_iso", "topk_iso_batch",
-    "topk_patterns", "hop_index", "hop_index_noalloc", "set_time_budget", "tune_cliques", "Server", "Result", "LIB_PATH", "EXPORTS",
+    "topk_patterns", "hop_index", "hop_index_noalloc", "set_time_budget", "tune_cliques", "Server",
+    "request_bytes", "topk_batch", "Result", "LIB_PATH", "EXPORTS",
     "RANK_SIZE", "RANK_WEIGHT_SUM", "RANK_DEGREE_SUM", "RANK_MNI",
 ]
 
@@ -28,7 +29,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libnuri.so")
 
 OK, ERR_INVALID, ERR_OOM, ERR_LIMIT, ERR_TIMEOUT, ERR_CANCELLED, ERR_CUDA, PENDING = range(8)
-REQ_CLIQUES, REQ_ISO = 0, 1
+REQ_CLIQUES, REQ_ISO, REQ_PATTERNS = 0, 1, 2
 RANK_SIZE, RANK_WEIGHT_SUM, RANK_DEGREE_SUM, RANK_MNI = range(4)
 LOAD_DEVICE_INPUT, LOAD_NO_ISO = 0x1, 0x2
 CLIQUE_ALL, CLIQUE_MAXIMAL = 0x0, 0x1
@@ -42,7 +43,8 @@ EXPORTS = (
     "nuri_free_result", "nuri_last_error", "nuri_version", "nuri_set_time_budget",
     "nuri_tune_cliques",
     "nuri_server_create", "nuri_server_submit", "nuri_server_poll", "nuri_server_wait",
-    "nuri_server_stats", "nuri_server_destroy",
+    "nuri_server_stats", "nuri_server_budget", "nuri_server_destroy", "nuri_request_bytes",
+    "nuri_topk_batch", "nuri_server_clique_stats", "nuri_set_partition", "nuri_seed_part",
 )
 
 
@@ -62,7 +64,7 @@ class _Stats(ctypes.Structure):
         ("device_ms", ctypes.c_double), ("launches", ctypes.c_int64),
         ("expand_launches", ctypes.c_int64), ("expand_ms", ctypes.c_double),
         ("tail_launches", ctypes.c_int64), ("tail_ms", ctypes.c_double),
-        ("tail_words", ctypes.c_int64),
+        ("tail_words", ctypes.c_int64), ("dense_records", ctypes.c_int64 * 3),
     ]
 
 
@@ -86,7 +88,8 @@ class _Query(ctypes.Structure):
 
 class _Request(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("k", ctypes.c_int32), ("rank", ctypes.c_int32),
-                ("flags", ctypes.c_uint32), ("query", _Query)]
+                ("flags", ctypes.c_uint32), ("query", _Query),
+                ("pattern_edges", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class _ServerCfg(ctypes.Structure):
@@ -96,7 +99,8 @@ class _ServerCfg(ctypes.Structure):
 
 class _Times(ctypes.Structure):
     _fields_ = [("queue_ms", ctypes.c_double), ("service_ms", ctypes.c_double),
-                ("total_ms", ctypes.c_double)]
+                ("total_ms", ctypes.c_double), ("start_ms", ctypes.c_double),
+                ("done_ms", ctypes.c_double), ("mem_bytes", ctypes.c_int64)]
 
 
 class _Info(ctypes.Structure):
@@ -161,6 +165,22 @@ def lib():
             L.nuri_server_stats.argtypes = [P, ctypes.POINTER(ctypes.c_int64),
                                             ctypes.POINTER(ctypes.c_int64)]
             L.nuri_server_stats.restype = i32
+            L.nuri_set_partition.argtypes = [P, P]
+            L.nuri_set_partition.restype = i32
+            L.nuri_seed_part.argtypes = [i32, i32]
+            L.nuri_seed_part.restype = i32
+            L.nuri_topk_batch.argtypes = [P, i32, ctypes.POINTER(_Request), P,
+                                          ctypes.POINTER(ctypes.POINTER(_Result))]
+            L.nuri_topk_batch.restype = i32
+            L.nuri_server_clique_stats.argtypes = [P, ctypes.POINTER(ctypes.c_int64),
+                                                   ctypes.POINTER(ctypes.c_int64)]
+            L.nuri_server_clique_stats.restype = i32
+            L.nuri_server_budget.argtypes = [P, ctypes.POINTER(ctypes.c_int64),
+                                             ctypes.POINTER(ctypes.c_int64)]
+            L.nuri_server_budget.restype = i32
+            L.nuri_request_bytes.argtypes = [P, ctypes.POINTER(_Request),
+                                             ctypes.POINTER(ctypes.c_int64)]
+            L.nuri_request_bytes.restype = i32
             L.nuri_server_destroy.argtypes = [P]
             L.nuri_server_destroy.restype = None
             L.nuri_free_result.argtypes = [ctypes.POINTER(_Result)]
@@ -224,6 +244,7 @@ def _unpack(rp) -> Result:
             out.append((int(score[i]), lab, e))
     s = r.stats
     out.stats = {f: getattr(s, f) for f, _ in _Stats._fields_ if f != "pad"}
+    out.stats["dense_records"] = list(out.stats["dense_records"])
     lib().nuri_free_result(rp)
     return out
 
@@ -322,6 +343,39 @@ def topk_iso_batch(g: Graph, queries, ks, degree_rank=False, keep_ties=False,
     return [_unpack(outs[i]) for i in range(nq)]
 
 
+def _request(req, keep):
+    """A request tuple as the C struct: ("clique", k[, maximal[, keep_ties]]),
+    ("iso", query, k[, degree_rank[, keep_ties]]) or ("patterns", M, k[, keep_ties])."""
+    kind = req[0]
+    if kind == "clique":
+        k = req[1]
+        flags = (CLIQUE_MAXIMAL if len(req) > 2 and req[2] else 0) | \
+            (KEEP_TIES if len(req) > 3 and req[3] else 0)
+        return _Request(REQ_CLIQUES, int(k), RANK_SIZE, flags, _Query(0, 0, None, None, None),
+                        0, 0)
+    if kind == "iso":
+        q, k = req[1], req[2]
+        rank = RANK_DEGREE_SUM if len(req) > 3 and req[3] else RANK_WEIGHT_SUM
+        flags = KEEP_TIES if len(req) > 4 and req[4] else 0
+        return _Request(REQ_ISO, int(k), rank, flags, _query_struct(q, keep), 0, 0)
+    if kind == "patterns":
+        M, k = req[1], req[2]
+        flags = KEEP_TIES if len(req) > 3 and req[3] else 0
+        return _Request(REQ_PATTERNS, int(k), RANK_MNI, flags, _Query(0, 0, None, None, None),
+                        int(M), 0)
+    raise ValueError(kind)
+
+
+def topk_batch(g: Graph, requests, stream=None) -> list:
+    """Requests of any kind in one nuri_topk_batch call (see _request for the tuples)."""
+    keep = []
+    n = len(requests)
+    arr = (_Request * max(n, 1))(*[_request(r, keep) for r in requests])
+    outs = (ctypes.POINTER(_Result) * max(n, 1))()
+    _check(lib().nuri_topk_batch(g.handle, n, arr, _stream(stream), outs))
+    return [_unpack(outs[i]) for i in range(n)]
+
+
 def topk_patterns(g: Graph, M: int, k: int, stream=None) -> Result:
     rp = ctypes.POINTER(_Result)()
     _check(lib().nuri_topk_patterns(g.handle, int(M), int(k), RANK_MNI, 0, _stream(stream),
@@ -346,6 +400,20 @@ def hop_index_noalloc(n, off, adj, nnz, labels, L, score, hops, out, stream=None
                                         int(hops), out, _stream(stream)))
 
 
+def _times(tm):
+    return {f: getattr(tm, f) for f, _ in _Times._fields_}
+
+
+def request_bytes(g: Graph, kind, k, query=None, maximal=False) -> int:
+    """Device bytes the server admits a request with (nuri_request_bytes); kind is
+    "clique" or "iso"."""
+    keep = []
+    r = _request(("clique", k, maximal) if kind == "clique" else ("iso", query, k), keep)
+    b = ctypes.c_int64()
+    _check(lib().nuri_request_bytes(g.handle, ctypes.byref(r), ctypes.byref(b)))
+    return b.value
+
+
 class Server:
     """Continuous-batching request server over a resident graph (nuri_server_*)."""
 
@@ -357,19 +425,23 @@ class Server:
         self._h = h
 
     def submit_cliques(self, k, maximal=False) -> int:
-        r = _Request(REQ_CLIQUES, int(k), RANK_SIZE, CLIQUE_MAXIMAL if maximal else 0,
-                     _Query(0, 0, None, None, None))
+        r = _request(("clique", k, maximal), [])
         t = ctypes.c_uint64()
         _check(lib().nuri_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
         return t.value
 
     def submit_iso(self, q, k, degree_rank=False) -> int:
         keep = []
-        r = _Request(REQ_ISO, int(k), RANK_DEGREE_SUM if degree_rank else RANK_WEIGHT_SUM, 0,
-                     _query_struct(q, keep))
+        r = _request(("iso", q, k, degree_rank), keep)
         t = ctypes.c_uint64()
         _check(lib().nuri_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
         return t.value
+
+    def budget(self):
+        """(budget bytes, bytes held for the whole run)."""
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().nuri_server_budget(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
 
     def poll(self, ticket):
         """(result, times) when finished, None while pending; raises on a failed request."""
@@ -380,21 +452,22 @@ class Server:
         if rc == PENDING:
             return None
         _check(rc)
-        return _unpack(rp), {"queue_ms": tm.queue_ms, "service_ms": tm.service_ms,
-                             "total_ms": tm.total_ms}
+        return _unpack(rp), _times(tm)
 
     def wait(self, ticket):
         rp = ctypes.POINTER(_Result)()
         tm = _Times()
         _check(lib().nuri_server_wait(self._h, ctypes.c_uint64(ticket), ctypes.byref(rp),
                                       ctypes.byref(tm)))
-        return _unpack(rp), {"queue_ms": tm.queue_ms, "service_ms": tm.service_ms,
-                             "total_ms": tm.total_ms}
+        return _unpack(rp), _times(tm)
 
     def stats(self):
         a, b = ctypes.c_int64(), ctypes.c_int64()
         _check(lib().nuri_server_stats(self._h, ctypes.byref(a), ctypes.byref(b)))
-        return {"iso_batches": a.value, "iso_batched_requests": b.value}
+        c, d = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().nuri_server_clique_stats(self._h, ctypes.byref(c), ctypes.byref(d)))
+        return {"iso_batches": a.value, "iso_batched_requests": b.value,
+                "clique_searches": c.value, "clique_requests": d.value}
 
     def close(self):
         if self._h:

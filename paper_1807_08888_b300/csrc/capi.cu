@@ -5,7 +5,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <new>
+#include <utility>
+#include <vector>
 
 #include "nuri_internal.cuh"
 
@@ -206,6 +209,170 @@ nuri_status nuri_topk_patterns(nuri_graph* g, int32_t M, int32_t k, int32_t rank
     topk_patterns(g, M, k, flags, (cudaStream_t)stream, out);
   });
 }
+
+}  // extern "C"
+
+namespace nuri {
+namespace {
+
+// The first `count` rows of r, or, when count < 0, the rows whose score is at least
+// `min_score`; a new result with r's kind and counters.
+nuri_result* slice_result(const nuri_result* r, int32_t count, int64_t min_score) {
+  if (count < 0) {
+    count = 0;
+    while (count < r->count && r->score[count] >= min_score) ++count;
+  }
+  count = std::min(count, r->count);
+  const int64_t nv = r->vert_off[count], ne = r->edge_off[count];
+  nuri_result* o = new_result(r->kind, count, nv, ne, r->labels != nullptr);
+  memcpy(o->score, r->score, sizeof(int64_t) * count);
+  memcpy(o->vert_off, r->vert_off, sizeof(int32_t) * (count + 1));
+  memcpy(o->edge_off, r->edge_off, sizeof(int32_t) * (count + 1));
+  memcpy(o->verts, r->verts, sizeof(int32_t) * nv);
+  memcpy(o->edges, r->edges, sizeof(int32_t) * 2 * ne);
+  if (r->labels) memcpy(o->labels, r->labels, sizeof(int32_t) * nv);
+  o->stats = r->stats;
+  return o;
+}
+
+// A connected simple query of 1..8 vertices (the isomorphism engine's precondition).
+bool query_ok(const nuri_query& q) {
+  if (q.nq < 1 || q.nq > 8 || q.ne < 0 || !q.labels || (q.ne > 0 && (!q.src || !q.dst)))
+    return false;
+  uint32_t adj[8] = {};
+  for (int e = 0; e < q.ne; ++e) {
+    const int a = q.src[e], b = q.dst[e];
+    if (a < 0 || b < 0 || a >= q.nq || b >= q.nq || a == b) return false;
+    adj[a] |= 1u << b;
+    adj[b] |= 1u << a;
+  }
+  uint32_t seen = 1, frontier = 1;
+  while (frontier) {
+    uint32_t nxt = 0;
+    for (int v = 0; v < q.nq; ++v)
+      if ((frontier >> v) & 1) nxt |= adj[v];
+    frontier = nxt & ~seen;
+    seen |= nxt;
+  }
+  return seen == (1u << q.nq) - 1;
+}
+
+// Requests of one shared-work group (same kind and key), answered by one run of the
+// largest k: cliques and patterns.
+template <class Run>
+void run_prefix_group(const std::vector<int>& idx, const nuri_request* reqs, uint32_t flags,
+                      Run&& run, nuri_result** outs) {
+  int32_t K = 0;
+  for (int i : idx) K = std::max(K, reqs[i].k);
+  nuri_result* r = nullptr;
+  run(K, flags, &r);
+  struct Free {
+    nuri_result* r;
+    ~Free() { nuri_free_result(r); }
+  } guard{r};
+  const bool ties = flags & NURI_KEEP_TIES;
+  for (int i : idx) {
+    const int32_t k = reqs[i].k;
+    if (!ties) outs[i] = slice_result(r, k, 0);
+    else if (r->count < k) outs[i] = slice_result(r, r->count, 0);
+    else outs[i] = slice_result(r, -1, r->score[k - 1]);  // every row tied with the k-th
+  }
+}
+
+}  // namespace
+}  // namespace nuri
+
+extern "C" {
+
+nuri_status nuri_topk_batch(nuri_graph* g, int32_t nreq, const nuri_request* reqs,
+                            void* stream, nuri_result** outs) {
+  return guarded([&] {
+    if (!g || !reqs || !outs || nreq < 0) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_batch: NULL argument");
+    for (int i = 0; i < nreq; ++i) outs[i] = nullptr;
+    for (int i = 0; i < nreq; ++i) {
+      const nuri_request& r = reqs[i];
+      if (r.k < 1) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_batch: request %d has k < 1", i);
+      if (r.kind == NURI_REQ_CLIQUES) {
+        if (r.rank != NURI_RANK_SIZE) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_batch: request %d: clique rank must be NURI_RANK_SIZE", i);
+      } else if (r.kind == NURI_REQ_ISO) {
+        if (r.rank != NURI_RANK_WEIGHT_SUM && r.rank != NURI_RANK_DEGREE_SUM)
+          NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_batch: request %d: bad isomorphism rank", i);
+        if (!query_ok(r.query)) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_batch: request %d: bad query", i);
+        if (!g->d.labels || !g->d.lsoff) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_batch: graph has no labels");
+        if (r.rank == NURI_RANK_WEIGHT_SUM && !g->d.weights)
+          NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_batch: graph has no weights");
+      } else if (r.kind == NURI_REQ_PATTERNS) {
+        if (r.rank != NURI_RANK_MNI) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_batch: request %d: pattern rank must be NURI_RANK_MNI", i);
+        if (r.pattern_edges < 1 || r.pattern_edges > 5)
+          NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_batch: request %d: M must be 1..5", i);
+        if (!g->d.labels || !g->d.lsoff) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_batch: graph has no labels");
+      } else {
+        NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_batch: request %d has an unknown kind", i);
+      }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    // groups: (kind, key) -> request indices, in first-appearance order
+    std::vector<std::pair<std::pair<int, uint64_t>, std::vector<int>>> groups;
+    for (int i = 0; i < nreq; ++i) {
+      const nuri_request& r = reqs[i];
+      uint64_t key = r.flags;
+      if (r.kind == NURI_REQ_ISO) key |= (uint64_t)(uint32_t)r.rank << 32;
+      if (r.kind == NURI_REQ_PATTERNS) key |= (uint64_t)(uint32_t)r.pattern_edges << 32;
+      auto it = std::find_if(groups.begin(), groups.end(), [&](const auto& x) {
+        return x.first.first == r.kind && x.first.second == key;
+      });
+      if (it == groups.end()) groups.push_back({{r.kind, key}, {i}});
+      else it->second.push_back(i);
+    }
+    try {
+      for (auto& grp : groups) {
+        const std::vector<int>& idx = grp.second;
+        const nuri_request& r0 = reqs[idx[0]];
+        if (r0.kind == NURI_REQ_CLIQUES) {
+          run_prefix_group(idx, reqs, r0.flags, [&](int32_t K, uint32_t fl, nuri_result** o) {
+            topk_cliques(g, K, fl, 0, s, o);
+          }, outs);
+        } else if (r0.kind == NURI_REQ_PATTERNS) {
+          run_prefix_group(idx, reqs, r0.flags, [&](int32_t K, uint32_t fl, nuri_result** o) {
+            topk_patterns(g, r0.pattern_edges, K, fl, s, o);
+          }, outs);
+        } else {
+          std::vector<nuri_query> qs;
+          std::vector<int32_t> ks;
+          for (int i : idx) {
+            qs.push_back(reqs[i].query);
+            ks.push_back(reqs[i].k);
+          }
+          std::vector<nuri_result*> res(idx.size(), nullptr);
+          topk_iso_batch(g, (int32_t)idx.size(), qs.data(), ks.data(), r0.rank, r0.flags, s,
+                         res.data());
+          for (size_t j = 0; j < idx.size(); ++j) outs[idx[j]] = res[j];
+        }
+      }
+    } catch (...) {
+      for (int i = 0; i < nreq; ++i) {
+        nuri_free_result(outs[i]);
+        outs[i] = nullptr;
+      }
+      throw;
+    }
+  });
+}
+
+nuri_status nuri_set_partition(nuri_graph* g, const nuri_partition* p) {
+  return guarded([&] {
+    if (!g) NURI_FAIL(NURI_ERR_INVALID, "nuri_set_partition: NULL graph");
+    if (!p || p->count == 1) {
+      g->part = nuri_partition{0, 1, nullptr, nullptr};
+      return;
+    }
+    if (p->count < 1 || p->index < 0 || p->index >= p->count)
+      NURI_FAIL(NURI_ERR_INVALID, "nuri_set_partition: need 0 <= index < count");
+    g->part = *p;
+  });
+}
+
+int32_t nuri_seed_part(int32_t v, int32_t count) { return seed_part(v, count); }
 
 nuri_status nuri_set_time_budget(double ms) {
   return guarded([&] {

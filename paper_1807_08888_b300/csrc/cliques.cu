@@ -313,6 +313,51 @@ __device__ __forceinline__ void colour_class(unsigned long long* cls, unsigned l
   }
 }
 
+// Core filter of a record's candidates (warp-cooperative): rows[i*W .. i*W+W) is the adjacency
+// of candidate i among the p candidates.  Candidates with fewer than need - 1 neighbours among
+// the kept ones are dropped, repeatedly, until every kept candidate has enough (the (need-1)-
+// core of P); a dropped candidate's row is cleared and its bit removed from every row.
+// Returns the number kept.  alive: W words of shared memory.
+template <int W>
+__device__ int core_peel(unsigned long long* rows, int p, int need, unsigned long long* alive,
+                         int lane) {
+  const unsigned FULL = 0xffffffffu;
+  if (lane < W) {
+    const int lo = lane * 64;
+    alive[lane] = p >= lo + 64 ? ~0ull : (p > lo ? (1ull << (p - lo)) - 1 : 0ull);
+  }
+  __syncwarp();
+  bool any_removed = false;
+  while (true) {
+    bool removed = false;
+    for (int i = lane; i < p; i += 32) {
+      if (!((alive[i >> 6] >> (i & 63)) & 1ull)) continue;
+      int d = 0;
+#pragma unroll
+      for (int q = 0; q < W; ++q) d += __popcll(rows[i * W + q] & alive[q]);
+      if (d < need - 1) {
+        atomicAnd(&alive[i >> 6], ~(1ull << (i & 63)));
+        removed = true;
+      }
+    }
+    __syncwarp();
+    if (!__any_sync(FULL, removed)) break;
+    any_removed = true;
+  }
+  if (any_removed) {
+    for (int i = lane; i < p; i += 32) {
+      const bool a = (alive[i >> 6] >> (i & 63)) & 1ull;
+#pragma unroll
+      for (int q = 0; q < W; ++q) rows[i * W + q] = a ? (rows[i * W + q] & alive[q]) : 0ull;
+    }
+  }
+  int c = 0;
+#pragma unroll
+  for (int q = 0; q < W; ++q) c += __popcll(alive[q]);
+  __syncwarp();
+  return c;
+}
+
 // out = a & row over words [0, wa) (the words at and above wa are zero in a), paired loads.
 template <int W>
 __device__ __forceinline__ void and_live(unsigned long long* out, const unsigned long long* a,
@@ -342,6 +387,11 @@ __device__ __forceinline__ void and_live(unsigned long long* out, const unsigned
 // next wave spreads that subtree over the GPU instead of leaving it to one lane.
 // ---------------------------------------------------------------------------------------------
 constexpr int TPICKS = 28;  // vertices a task can hold below its record
+// Device memory bounds of one query's buffers (they make the server's admission estimate an
+// upper bound): records handed to the dense tiers or sent back per round, and the dense store
+constexpr int64_t kRoundRecs = 1 << 16;
+constexpr int64_t kDefaultFrontier = 1 << 20;  // device frontier records before spilling
+constexpr int64_t kStoreBytes = 256ll << 20;
 
 struct WTask {
   int32_t slot;
@@ -705,6 +755,7 @@ __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
   __shared__ int32_t sCnt[NW][BMW];
   __shared__ uint16_t sPerm[NW][BMW], sInv[NW][BMW];
   __shared__ int32_t sTot[NW], sNext[NW];
+  __shared__ unsigned long long sAlive[NW][W];     // core filter: candidates kept
   extern __shared__ unsigned long long dynrows[];  // NW * BMW * W words: adjacency rows of P
 
   const int lane = threadIdx.x & 31;
@@ -923,7 +974,14 @@ __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
       uint16_t* inv = sInv[w];    // index in sp -> new index
       for (int i = lane; i < p; i += 32) dg[i] = 0;
       __syncwarp();
-      for (int pass = 0; pass < 2; ++pass) {
+      // candidates a clique reaching tau needs below this record (0: no core filter)
+      int core_need = 0;
+      if (!cx.no_prune) {
+        const int32_t t_now = ld_volatile(&cx.st->tau);
+        if (t_now != INT32_MIN && t_now - nv > 1) core_need = t_now - nv;
+      }
+      int pass = 0;
+      for (; pass < 2; ++pass) {
         if (pass == 1) {
           for (int i = lane; i < p * W; i += 32) rows[i] = 0;
           __syncwarp();
@@ -954,6 +1012,15 @@ __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
           if (lane == 0) my_bytes += 4ull * (unsigned long long)(scanned < re - rb ? scanned : re - rb);
         }
         __syncwarp();
+        if (pass == 0 && core_need > 1) {
+          // a clique of size >= tau below this record has at least core_need = tau - |V|
+          // members in P, each with at least core_need - 1 neighbours in P: with fewer such
+          // candidates the record holds no result (the record itself was handled above)
+          int c = 0;
+          for (int i = lane; i < p; i += 32) c += dg[i] >= core_need - 1 ? 1 : 0;
+          for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
+          if (c < core_need) break;
+        }
         if (pass == 0 && lane == 0) {
           // counting sort by degree, descending (ties: lower index first)
           uint16_t* bucket = sCol[w];
@@ -972,6 +1039,22 @@ __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
           }
         }
         __syncwarp();
+      }
+      if (pass < 2) {  // rejected by the degree count
+        if (lane == 0) ++my_pruned;
+        continue;
+      }
+      // core filter on the rows: candidates with fewer than core_need - 1 neighbours among the
+      // remaining ones cannot be in a clique reaching tau; they are removed (rows cleared, bits
+      // dropped from every row) until every remaining candidate has enough, and the record is
+      // dropped if fewer than core_need remain.  Removed candidates stay as isolated vertices:
+      // their colour bound (|V| + 1 < tau) prunes them at once.
+      if (core_need > 1) {
+        const int alive = core_peel<W>(rows, p, core_need, sAlive[w], lane);
+        if (alive < core_need) {
+          if (lane == 0) ++my_pruned;
+          continue;
+        }
       }
       // record-level colouring (index order) and the order of the children by colour
       uint16_t* ord = sOrd[w];   // vertices by ascending colour
@@ -1422,13 +1505,22 @@ __device__ __forceinline__ int bucket_of(int32_t bound) { return bound >= NB - 1
 // narrow bitmap tail (|N+(v)| <= 64).  Seeds are consumed class 1 first, each class in
 // descending bound order: the narrow seeds are cheap and usually raise tau to its final
 // value (planted or core cliques), so the wide, dense seeds are searched under a high tau.
-__global__ void k_seed_bounds(DevGraph g, int32_t* keys, int32_t* vals) {
+// With a seed partition, seeds of other parts get key 0 (class 0, bound 0): they sort last and
+// are never taken (every real seed's bound is at least 1).
+__global__ void k_seed_bounds(DevGraph g, int32_t part_index, int32_t part_count, int32_t* keys,
+                              int32_t* vals) {
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < g.n;
        r += (int64_t)gridDim.x * blockDim.x) {
     int32_t outdeg = (int32_t)(g.ooff[r + 1] - g.ooff[r]);
-    keys[r] = ((outdeg <= 64 ? 1 : 0) << 24) | (1 + outdeg);
+    const bool mine = part_count <= 1 || seed_part(g.vert_of[r], part_count) == part_index;
+    keys[r] = mine ? (((outdeg <= 64 ? 1 : 0) << 24) | (1 + outdeg)) : 0;
     vals[r] = (int32_t)r;
   }
+}
+
+// Raise tau to at least v (a threshold another part of a partitioned query published).
+__global__ void k_raise_tau(int32_t* tau, int32_t v) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) atomicMax(tau, v);
 }
 
 __global__ void k_bucket_hist(const int32_t* keys, int64_t n, int32_t* hist) {
@@ -1443,9 +1535,20 @@ __global__ void k_stage_hist(const Rec* stage, int64_t cnt, int32_t* hist) {
     if (stage[i].nv > 0) atomicAdd(&hist[bucket_of(stage[i].bound)], 1);
 }
 
+// Are ranks a != b adjacent?  (the out-row of the lower rank holds the higher one)
+__device__ __forceinline__ bool adjacent_rank(const DevGraph& g, int32_t a, int32_t b) {
+  if (a > b) {
+    const int32_t t = a;
+    a = b;
+    b = t;
+  }
+  return contains64(g.oout, g.ooff[a], g.ooff[a + 1], b);
+}
+
 // Warm start for tau (all-cliques ranking): one warp per seed grows a clique greedily inside
-// the seed's candidates (always adding the candidate of largest degree, then keeping the
-// candidates adjacent to it) and publishes subset_tau of its size.  The cliques themselves
+// the seed's candidates (always adding the candidate with the most neighbours among the
+// remaining candidates when at most 64 remain, else the one of largest graph degree -- ties:
+// larger graph degree, then lower rank -- then keeping the candidates adjacent to it) and publishes subset_tau of its size.  The cliques themselves
 // are not recorded (the search finds them again); only the lower bound on the k-th best is
 // used, so the answer is unchanged.  buf: max_out entries per warp.
 __global__ void k_greedy_tau(DevGraph g, const int32_t* __restrict__ seeds, int64_t nseeds,
@@ -1463,20 +1566,28 @@ __global__ void k_greedy_tau(DevGraph g, const int32_t* __restrict__ seeds, int6
     __syncwarp();
     int c = 1;
     while (p > 0) {
-      // the candidate of largest degree (ties: lowest rank)
-      int best = -1, bestd = -1;
+      // the candidate with the most neighbours among the candidates; key = (that count,
+      // graph degree, -rank), compared as one 64-bit value
+      long long bestkey = -1;
+      int best = -1;
       for (int t = lane; t < p; t += 32) {
-        const int32_t d = __ldg(g.deg + __ldg(g.vert_of + P[t]));
-        if (d > bestd) {
-          bestd = d;
-          best = P[t];
+        const int32_t x = P[t];
+        int inner = 0;
+        if (p <= 64)  // narrow candidate sets only: p^2 adjacency tests a step
+          for (int u = 0; u < p; ++u) inner += (u != t && adjacent_rank(g, x, P[u])) ? 1 : 0;
+        const int32_t d = min(__ldg(g.deg + __ldg(g.vert_of + x)), 0xFFFFF);
+        const long long key = ((long long)inner << 40) | ((long long)d << 20) |
+                              (long long)(0xFFFFF - (x & 0xFFFFF));
+        if (key > bestkey) {
+          bestkey = key;
+          best = x;
         }
       }
       for (int o = 16; o; o >>= 1) {
-        const int od = __shfl_xor_sync(FULL, bestd, o);
+        const long long ok = __shfl_xor_sync(FULL, bestkey, o);
         const int ob = __shfl_xor_sync(FULL, best, o);
-        if (od > bestd || (od == bestd && ob >= 0 && (best < 0 || ob < best))) {
-          bestd = od;
+        if (ok > bestkey || (ok == bestkey && ob >= 0 && (best < 0 || ob < best))) {
+          bestkey = ok;
           best = ob;
         }
       }
@@ -1600,15 +1711,35 @@ struct DenseBufs {
   DBuf<int32_t> vmap2, vmap4, vmap8, recV2, recV4, recV8, recN2, recN4, recN8, recP2, recP4,
       recP8;
   DBuf<unsigned long long> counters;  // [0] slots, [1] queue count, [2] next task
-  DBuf<WTask> qa, qb;
+  DBuf<WTask> qa, qb;                 // task queues (wave input and output), grown on demand
   DBuf<unsigned long long> low2, low4, low8;  // tie-aware pruning masks per slot
   DBuf<int32_t> reclow2, reclow4, reclow8;
   DBuf<int32_t> lexbuf;                      // smallest id of each size-tau result
   DBuf<unsigned long long> lexcnt;
   bool lex_allowed = false;  // all-cliques ranking, pruning on, ties not kept
-  int64_t qcap = 0;
+  int64_t qcap = 0;          // current entries of each queue
+  int64_t qmax = 0;          // entries a queue may grow to (NURI_TASK_QUEUE, default 16M)
   int32_t split_bits = 96;  // nodes with more candidates become tasks (measured best on B300)
 };
+
+// Entries each task queue may grow to (two queues): NURI_TASK_QUEUE, default 16M.
+int64_t task_queue_max() {
+  int64_t q = 1 << 24;
+  if (const char* e = getenv("NURI_TASK_QUEUE")) q = std::max<int64_t>(16, atoll(e));
+  return q;
+}
+
+// Device bytes of one store slot of the W-word tier (rows, vertex map, record, masks).
+int64_t slot_bytes(int W) {
+  const int64_t bmw = 64 * W;
+  return bmw * W * 8 + bmw * 4 + MAXD * 4 + 8 + W * 8 + 4;
+}
+
+// Store slots one dense pass uses at most: the records of a tier are searched in chunks of
+// this many (a chunk's task waves finish before the next chunk reuses the slots).
+int64_t slots_per_chunk(int W) {
+  return std::max<int64_t>(64, kStoreBytes / slot_bytes(W));
+}
 
 WideStore make_store(DenseBufs& B, int W, int64_t nrec, cudaStream_t s) {
   const int64_t bmw = 64 * W;
@@ -1632,12 +1763,17 @@ WideStore make_store(DenseBufs& B, int W, int64_t nrec, cudaStream_t s) {
     }
   }
   if (!B.counters.p) B.counters.alloc(3, s);
-  if (!B.qa.p) {
-    B.qcap = 1 << 24;  // 16M tasks per queue (about 3.2 GB each)
-    if (const char* e = getenv("NURI_TASK_QUEUE")) B.qcap = std::max<int64_t>(16, atoll(e));
-    B.qa.alloc(B.qcap, s);
-    B.qb.alloc(B.qcap, s);
+  if (B.qmax == 0) {
+    B.qmax = task_queue_max();
     if (const char* e = getenv("NURI_TASK_SPLIT")) B.split_bits = std::max(1, atoi(e));
+  }
+  // the record kernel queues up to one task per candidate of every record: start the queues
+  // at that size (at least 1M entries); the task waves grow them further when they fill up
+  const int64_t want = std::min<int64_t>(B.qmax, std::max<int64_t>(1 << 20, nrec * bmw));
+  if (B.qcap < want) {
+    B.qa.alloc(want, s);
+    B.qb.alloc(want, s);
+    B.qcap = want;
   }
   WideStore ws;
   ws.rows = rows.p;
@@ -1844,7 +1980,9 @@ void update_lex(const Ctx& cx, WideStore& ws, ResultStore& rs, DenseBufs& B, cud
 
 // Dense records of one width: the warp kernel stores them and queues their children, then
 // task waves run until the queue is empty.  A wave's grid is the resident capacity of the
-// task kernel (lanes take tasks dynamically).
+// task kernel (lanes take tasks dynamically).  Records are taken in chunks of at most
+// slots_per_chunk(W) so the store stays bounded; the queues grow (up to their maximum) when a
+// wave's output passes an eighth of their size, the point where splitting would stop.
 template <int W>
 int64_t run_dense(Ctx cx, const Rec* recs, int64_t nrec, int grid, size_t dyn, DenseBufs& B,
                   TailTime& tt, ResultStore& rs, cudaStream_t s) {
@@ -1858,59 +1996,78 @@ int64_t run_dense(Ctx cx, const Rec* recs, int64_t nrec, int grid, size_t dyn, D
       per_sm = 4;
     return per_sm * sm_count();
   }();
-  WideStore ws = make_store(B, W, nrec, s);
-  NURI_CUDA(cudaMemsetAsync(B.counters.p, 0, 3 * sizeof(unsigned long long), s));
-  NURI_CUDA(cudaMemsetAsync(&cx.st->work_next, 0, sizeof(int64_t), s));
-  k_clique_expand<W><<<grid, KCfg<W>::WARPS * 32, dyn, s>>>(cx, recs, nullptr, nrec, ws);
-  NURI_CUDA(cudaGetLastError());
-  ++launched;
-  WTask* in = B.qa.p;
-  WTask* out = B.qb.p;
-  bool timed = false;  // a wave's events are pending
-  while (true) {
-    unsigned long long cnt = 0;
-    NURI_CUDA(cudaMemcpyAsync(&cnt, B.counters.p + 1, 8, cudaMemcpyDeviceToHost, s));
-    NURI_CUDA(cudaStreamSynchronize(s));
-    if (timed) {
-      float ms = 0.f;
-      NURI_CUDA(cudaEventElapsedTime(&ms, tt.a, tt.b));
-      tt.ms += ms;
-      ++tt.launches;
-      timed = false;
-    }
-    int64_t n = std::min<int64_t>((int64_t)cnt, B.qcap);
-    if (n == 0) break;
-    compact_results(cx, rs, s);
-    if (B.lex_allowed) update_lex<W>(cx, ws, rs, B, s);
-    int32_t err = 0;
-    NURI_CUDA(cudaMemcpyAsync(&err, &cx.st->err, 4, cudaMemcpyDeviceToHost, s));
-    NURI_CUDA(cudaStreamSynchronize(s));
-    if (err & 4) break;  // out of time: the caller reports it
-    ws.q_out = out;
-    NURI_CUDA(cudaMemsetAsync(B.counters.p + 1, 0, 2 * sizeof(unsigned long long), s));
-    int tgrid = (int)std::min<int64_t>((n + 127) / 128, (int64_t)resident);
-    ws.in_next = B.counters.p + 2;
-    ws.in_n = n;
-    NURI_CUDA(cudaEventRecord(tt.a, s));
-    k_clique_tasks<W><<<tgrid, 128, 0, s>>>(cx, ws, in, n, B.counters.p + 2);
+  const int64_t chunk = slots_per_chunk(W);
+  for (int64_t c0 = 0; c0 < nrec; c0 += chunk) {
+    const int64_t cn = std::min<int64_t>(chunk, nrec - c0);
+    WideStore ws = make_store(B, W, cn, s);
+    NURI_CUDA(cudaMemsetAsync(B.counters.p, 0, 3 * sizeof(unsigned long long), s));
+    NURI_CUDA(cudaMemsetAsync(&cx.st->work_next, 0, sizeof(int64_t), s));
+    k_clique_expand<W><<<grid, KCfg<W>::WARPS * 32, dyn, s>>>(cx, recs + c0, nullptr, cn, ws);
     NURI_CUDA(cudaGetLastError());
-    NURI_CUDA(cudaEventRecord(tt.b, s));
-    timed = true;
-    if (trace) {
-      float ms = 0.f;
-      NURI_CUDA(cudaEventSynchronize(tt.b));
-      NURI_CUDA(cudaEventElapsedTime(&ms, tt.a, tt.b));
-      unsigned long long exp = 0;
-      int64_t nres = 0;
-      NURI_CUDA(cudaMemcpy(&exp, &cx.st->expansions, 8, cudaMemcpyDeviceToHost));
-      NURI_CUDA(cudaMemcpy(&nres, &cx.st->res_count, 8, cudaMemcpyDeviceToHost));
-      fprintf(stderr,
-              "[nuri]   dense W=%d wave %lld: %lld tasks, %.3f ms, nodes so far %llu, results "
-              "%lld of %lld\n",
-              W, (long long)launched, (long long)n, ms, exp, (long long)nres, (long long)rs.cap);
-    }
     ++launched;
-    std::swap(in, out);
+    bool in_is_a = true;  // the record kernel wrote its tasks to qa
+    bool timed = false;   // a wave's events are pending
+    while (true) {
+      unsigned long long cnt = 0;
+      NURI_CUDA(cudaMemcpyAsync(&cnt, B.counters.p + 1, 8, cudaMemcpyDeviceToHost, s));
+      NURI_CUDA(cudaStreamSynchronize(s));
+      if (timed) {
+        float ms = 0.f;
+        NURI_CUDA(cudaEventElapsedTime(&ms, tt.a, tt.b));
+        tt.ms += ms;
+        ++tt.launches;
+        timed = false;
+      }
+      int64_t n = std::min<int64_t>((int64_t)cnt, B.qcap);
+      if (n == 0) break;
+      if (n > B.qcap / 8 && B.qcap < B.qmax) {
+        // grow both queues, keeping the pending tasks
+        const int64_t cap = std::min<int64_t>(B.qmax, B.qcap * 4);
+        DBuf<WTask> na, nb;
+        na.alloc(cap, s);
+        nb.alloc(cap, s);
+        NURI_CUDA(cudaMemcpyAsync(na.p, in_is_a ? B.qa.p : B.qb.p, sizeof(WTask) * n,
+                                  cudaMemcpyDeviceToDevice, s));
+        B.qa = std::move(na);
+        B.qb = std::move(nb);
+        B.qcap = cap;
+        ws.q_cap = cap;
+        in_is_a = true;
+      }
+      compact_results(cx, rs, s);
+      if (B.lex_allowed) update_lex<W>(cx, ws, rs, B, s);
+      int32_t err = 0;
+      NURI_CUDA(cudaMemcpyAsync(&err, &cx.st->err, 4, cudaMemcpyDeviceToHost, s));
+      NURI_CUDA(cudaStreamSynchronize(s));
+      if (err & 4) return launched;  // out of time: the caller reports it
+      WTask* in = in_is_a ? B.qa.p : B.qb.p;
+      ws.q_out = in_is_a ? B.qb.p : B.qa.p;
+      NURI_CUDA(cudaMemsetAsync(B.counters.p + 1, 0, 2 * sizeof(unsigned long long), s));
+      int tgrid = (int)std::min<int64_t>((n + 127) / 128, (int64_t)resident);
+      ws.in_next = B.counters.p + 2;
+      ws.in_n = n;
+      NURI_CUDA(cudaEventRecord(tt.a, s));
+      k_clique_tasks<W><<<tgrid, 128, 0, s>>>(cx, ws, in, n, B.counters.p + 2);
+      NURI_CUDA(cudaGetLastError());
+      NURI_CUDA(cudaEventRecord(tt.b, s));
+      timed = true;
+      if (trace) {
+        float ms = 0.f;
+        NURI_CUDA(cudaEventSynchronize(tt.b));
+        NURI_CUDA(cudaEventElapsedTime(&ms, tt.a, tt.b));
+        unsigned long long exp = 0;
+        int64_t nres = 0;
+        NURI_CUDA(cudaMemcpy(&exp, &cx.st->expansions, 8, cudaMemcpyDeviceToHost));
+        NURI_CUDA(cudaMemcpy(&nres, &cx.st->res_count, 8, cudaMemcpyDeviceToHost));
+        fprintf(stderr,
+                "[nuri]   dense W=%d wave %lld: %lld tasks (queue %lld), %.3f ms, nodes so far "
+                "%llu, results %lld of %lld\n",
+                W, (long long)launched, (long long)n, (long long)B.qcap, ms, exp,
+                (long long)nres, (long long)rs.cap);
+      }
+      ++launched;
+      in_is_a = !in_is_a;
+    }
   }
   return launched;
 }
@@ -1920,7 +2077,7 @@ int64_t run_dense(Ctx cx, const Rec* recs, int64_t nrec, int grid, size_t dyn, D
 int64_t launch_expand(Ctx cx, const Rec* in, const int32_t* seeds, int64_t nin, int grid,
                       DBuf<Rec>& wide, DBuf<Rec>& mid, DBuf<Rec>& small, DenseBufs& B,
                       TailTime& tt, ResultStore& rs, cudaEvent_t ev0, cudaEvent_t ev1,
-                      cudaStream_t s) {
+                      int64_t* tier_recs, cudaStream_t s) {
   const size_t dyn1 = sizeof(unsigned long long) * KCfg<1>::WARPS * 64;
   const size_t dyn2 = sizeof(unsigned long long) * KCfg<2>::WARPS * 64 * 2 * 2;
   const size_t dyn4 = sizeof(unsigned long long) * KCfg<4>::WARPS * 64 * 4 * 4;
@@ -1944,6 +2101,9 @@ int64_t launch_expand(Ctx cx, const Rec* in, const int32_t* seeds, int64_t nin, 
   NURI_CUDA(cudaMemcpyAsync(counts, &cx.st->wide_count, 24, cudaMemcpyDeviceToHost, s));
   NURI_CUDA(cudaStreamSynchronize(s));
   int64_t launched = 1;
+  tier_recs[0] += counts[2];
+  tier_recs[1] += counts[1];
+  tier_recs[2] += counts[0];
   if (counts[2] > 0) {
     compact_results(cx, rs, s);
     launched += run_dense<2>(cx, small.p, counts[2], grid, dyn2, B, tt, rs, s);
@@ -1970,6 +2130,57 @@ struct HostBucket {
 }  // namespace
 
 // ---------------------------------------------------------------------------------------------
+// Upper bound of the device memory one top-k clique query allocates on graph G (the buffers of
+// topk_cliques below, at their bounded sizes): seeds and their sort, warm start, staging,
+// frontier buckets up to frontier_cap records, round arrays, split-tier scratch, dense stores
+// and task queues at their maximum, the initial result set twice (compaction) and the final
+// merge.  A result set that outgrows its initial size adds to this (rare; the set is
+// compacted to the rows >= tau first).
+int64_t clique_query_bytes(const nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap) {
+  const DevGraph& g = G->d;
+  const bool no_prune = flags & NURI_NO_PRUNE;
+  if (frontier_cap <= 0) frontier_cap = kDefaultFrontier;
+  const int64_t rec = sizeof(Rec);
+  const int64_t total_warps = (int64_t)sm_count() * 6 * KCfg<1>::WARPS;
+  const int64_t n = std::max(g.n, 1);
+  int64_t b = 0;
+  b += 4 * n * 4 + 2 * n * 8 + 2 * NB * 4;                              // seeds, sort temp
+  b += (int64_t)sm_count() * 4 * 8 * std::max(g.max_out, 1) * 4;       // warm start
+  b += std::max<int64_t>(1 << 16, (int64_t)g.max_out * 8) * rec;        // staging
+  if (g.max_out > PSMEM) b += total_warps * g.max_out * 4;              // P scratch
+  if (g.max_out > 64 * KWIDE && !no_prune) b += total_warps * CB_ROWS * CB_W * 8;
+  b += frontier_cap * rec + (int64_t)sizeof(BucketPtrs);                // frontier buckets
+  b += 4 * kRoundRecs * rec + std::max<int64_t>(total_warps * 2, 4096) * rec;
+  const int64_t res = std::max<int64_t>(1 << 16, (int64_t)k * 64);
+  b += 2 * res * rec + res * (MAXD * 4 + 4 * 6 + 8);                   // results, merge
+  if (g.max_out > 64) {                                                 // dense tiers
+    for (int W : {2, 4, KWIDE}) b += slots_per_chunk(W) * slot_bytes(W);
+    b += 2 * task_queue_max() * (int64_t)sizeof(WTask);
+  }
+  return b;
+}
+
+// Local memory the driver reserves, once per context, for the clique kernels: their largest
+// per-thread frame times the threads the device can hold at once.
+int64_t clique_local_reserve_bytes() {
+  size_t frame = 0;
+  auto take = [&](const void* f) {
+    cudaFuncAttributes a;
+    if (cudaFuncGetAttributes(&a, f) == cudaSuccess) frame = std::max(frame, a.localSizeBytes);
+  };
+  take((const void*)k_clique_tasks<2>);
+  take((const void*)k_clique_tasks<4>);
+  take((const void*)k_clique_tasks<KWIDE>);
+  take((const void*)k_clique_expand<1>);
+  take((const void*)k_clique_expand<2>);
+  take((const void*)k_clique_expand<4>);
+  take((const void*)k_clique_expand<KWIDE>);
+  int dev = 0, threads = 2048;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&threads, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+  return (int64_t)frame * sm_count() * threads;
+}
+
 void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap,
                   cudaStream_t s, nuri_result** out) {
   int64_t launches = 0;
@@ -1978,7 +2189,7 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
   const bool maximal = flags & NURI_CLIQUE_MAXIMAL;
   const bool no_prune = flags & NURI_NO_PRUNE;
   const bool keep_ties = flags & NURI_KEEP_TIES;
-  if (frontier_cap <= 0) frontier_cap = 1 << 22;
+  if (frontier_cap <= 0) frontier_cap = kDefaultFrontier;
   const int n = g.n;
 
   const int grid = sm_count() * 6;  // CTAs of the narrow kernel: 6 x 4 warps per SM
@@ -2023,7 +2234,7 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
   std::vector<int32_t> seed_hist(2 * NB, 0);
   if (n > 0) {
     ++launches;
-    k_seed_bounds<<<grid_for(n), 256, 0, s>>>(g, skeys.p, svals.p);
+    k_seed_bounds<<<grid_for(n), 256, 0, s>>>(g, G->part.index, G->part.count, skeys.p, svals.p);
     size_t tb = 0;
     cub::DeviceRadixSort::SortPairsDescending(nullptr, tb, skeys.p, skeys2.p, svals.p, svals2.p,
                                               n, 0, 32, s);
@@ -2059,9 +2270,9 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
     gtau.alloc(1, s);
     const int32_t neg = INT32_MIN;
     NURI_CUDA(cudaMemcpyAsync(gtau.p, &neg, 4, cudaMemcpyHostToDevice, s));
-    const int64_t c0 = seed_lo[NB - 1], n0 = seed_hi[0] - c0;  // class 0 (wide) seeds
+    const int64_t c0 = seed_lo[NB - 1], n0 = seed_lo[0] - c0;  // class 0 (wide) seeds
     const int64_t n1 = seed_hi[NB];                             // class 1 (narrow) seeds
-    const int64_t take0 = std::min<int64_t>(n0, 4096), take1 = std::min<int64_t>(n1, 1024);
+    const int64_t take0 = std::min<int64_t>(n0, 4096), take1 = std::min<int64_t>(n1, 16384);
     if (take0 > 0) {
       ++launches;
       k_greedy_tau<<<gblocks, 256, 0, s>>>(g, svals2.p + c0, take0, k, gbuf.p, gtau.p);
@@ -2107,9 +2318,10 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
       b.spilled_n.clear();
       b.spilled_total = 0;
     }
-    // one cursor per seed class; a chunk may run across bound buckets
+    // one cursor per seed class; a chunk may run across bound buckets.  Bucket 0 of class 0
+    // holds only the seeds of other parts (bound 0) and is never taken.
     int64_t cls_next[2] = {seed_lo[NB - 1], seed_lo[NB + NB - 1]};
-    const int64_t cls_end[2] = {seed_hi[0], seed_hi[NB]};
+    const int64_t cls_end[2] = {seed_lo[0], seed_hi[NB]};
     auto bucket_at = [&](int c, int64_t pos) {
       for (int b = NB - 1; b >= 0; --b)
         if (pos < seed_hi[c * NB + b]) return b;
@@ -2134,6 +2346,15 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
     // smaller split limit (exercises the frontier tier in tests)
     if (const char* e = getenv("NURI_SPLIT_ABOVE")) cx.split_above = std::max(1, atoi(e));
     int64_t rounds = 0;
+    // per-round arrays of records handed to the dense tiers or sent back (at most kRoundRecs)
+    auto ensure_round = [&](int64_t need) {
+      need = std::max<int64_t>(need, 4096);
+      if ((int64_t)deferred.n < need) deferred.alloc(need, s);
+      if ((int64_t)wide.n < need) wide.alloc(need, s);
+      if ((int64_t)mid.n < need) mid.alloc(need, s);
+      if ((int64_t)small.n < need) small.alloc(need, s);
+      cx.deferred = deferred.p;
+    };
     // the first chunk is small: with tau still unset every node is a result, so a wide first
     // launch would fill the result set with small cliques; the chunk doubles every seed round
     int64_t seed_chunk = 512;
@@ -2148,6 +2369,17 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
                   "visited, tau %d)",
                   (long long)rounds, (unsigned long long)hs.expansions, hs.tau);
       compact_results(cx, rs, s);
+      if (G->part.count > 1 && G->part.exchange) {
+        // partitioned query: publish this part's threshold, prune with the best one known
+        const int64_t loc = hs.tau == INT32_MIN ? INT64_MIN : (int64_t)hs.tau;
+        const int64_t glob = G->part.exchange(G->part.ctx, 0, loc);
+        if (glob > loc && glob <= MAXD + 1) {
+          k_raise_tau<<<1, 32, 0, s>>>(&st.p->tau, (int32_t)glob);
+          ++launches;
+          NURI_CUDA(cudaGetLastError());
+          hs.tau = (int32_t)glob;
+        }
+      }
       int32_t tau = hs.tau;
       // highest bucket with pending seeds (narrow class first) or frontier records
       int b_seed = -1, b_front = -1, seed_cls = -1;
@@ -2214,13 +2446,9 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
           h2.count -= take;
           nin += take;
         }
-        if ((int64_t)deferred.n < nin) deferred.alloc(std::max<int64_t>(nin, 4096), s);
-        if ((int64_t)wide.n < nin) wide.alloc(std::max<int64_t>(nin, 4096), s);
-        if ((int64_t)mid.n < nin) mid.alloc(std::max<int64_t>(nin, 4096), s);
-        if ((int64_t)small.n < nin) small.alloc(std::max<int64_t>(nin, 4096), s);
-        cx.deferred = deferred.p;
+        ensure_round(nin);
         launches += launch_expand(cx, inbuf.p, nullptr, nin, grid, wide, mid, small, dense, tail, rs, ev0,
-                                  ev1, s);
+                                  ev1, stats.dense_records, s);
         cx.res = rs.buf.p;
         cx.res_cap = rs.cap;
       } else {
@@ -2231,17 +2459,17 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
         // seeds that rank below the best frontier bucket
         if (!no_prune && tau > 0) hi = std::min(hi, seed_hi[c * NB + std::min(tau, NB - 1)]);
         if (!narrow_first && b_front >= 0) hi = std::min(hi, seed_hi[c * NB + b_front]);
+        // narrow seeds (at most 64 candidates) never reach the dense tiers nor the split, so
+        // their chunks are not bounded by the round arrays (unless a test lowers the split)
+        const bool narrow_only = c == 1 && cx.split_above >= 64;
+        if (!narrow_only) hi = std::min(hi, lo + kRoundRecs);
         hi = std::max(hi, std::min<int64_t>(lo + 1, cls_end[c]));
         nin = hi - lo;
         cls_next[c] = hi;
         seed_chunk = std::min<int64_t>(seed_chunk * 2, 1 << 20);
-        if ((int64_t)deferred.n < nin) deferred.alloc(std::max<int64_t>(nin, 4096), s);
-        if ((int64_t)wide.n < nin) wide.alloc(std::max<int64_t>(nin, 4096), s);
-        if ((int64_t)mid.n < nin) mid.alloc(std::max<int64_t>(nin, 4096), s);
-        if ((int64_t)small.n < nin) small.alloc(std::max<int64_t>(nin, 4096), s);
-        cx.deferred = deferred.p;
+        ensure_round(narrow_only ? 0 : nin);
         launches += launch_expand(cx, nullptr, svals2.p + lo, nin, grid, wide, mid, small, dense, tail, rs,
-                                  ev0, ev1, s);
+                                  ev0, ev1, stats.dense_records, s);
         cx.res = rs.buf.p;
         cx.res_cap = rs.cap;
       }

@@ -154,13 +154,20 @@ __device__ void refresh_tau(const IsoCtx& cx, int q, int64_t k, int32_t shift) {
   }
 }
 
-// Seeds: one per (query, vertex with the root's label); bound = score(v) + u.
+// Seeds: one per (query, vertex with the root's label); bound = score(v) + u.  With a seed
+// partition, the roots of other parts get the bound NONE (never expanded).
 __global__ void k_iso_seeds(IsoCtx cx, int32_t q, int64_t base, int64_t count, int32_t rootlab,
-                            long long* keys, unsigned long long* vals) {
+                            int32_t part_index, int32_t part_count, long long* keys,
+                            unsigned long long* vals) {
   const IsoQuery Q = cx.qs[q];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
        i += (int64_t)gridDim.x * blockDim.x) {
     int32_t v = cx.g.lab_vert[cx.g.lab_off[rootlab] + i];
+    vals[base + i] = ((unsigned long long)(uint32_t)q << 32) | (uint32_t)v;
+    if (part_count > 1 && seed_part(v, part_count) != part_index) {
+      keys[base + i] = NONE;
+      continue;
+    }
     long long b = __ldg(cx.vscore + v);
     for (int p = 1; p < Q.nq; ++p) {
       long long x = index_value(cx, v, Q.hop[p], Q.lab[p]);
@@ -171,8 +178,12 @@ __global__ void k_iso_seeds(IsoCtx cx, int32_t q, int64_t base, int64_t count, i
       b += x;
     }
     keys[base + i] = b;
-    vals[base + i] = ((unsigned long long)(uint32_t)q << 32) | (uint32_t)v;
   }
+}
+
+// Raise query q's threshold to at least v (published by another part of a partitioned run).
+__global__ void k_iso_raise_tau(IsoState* st, int32_t q, long long v) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) atomicMax(&st[q].tau, v);
 }
 
 __device__ void add_results_leaf(const IsoCtx& cx, int q, const IsoQuery& Q, bool valid,
@@ -576,6 +587,17 @@ bool prepare_query(const nuri_query& in, int32_t k, const std::vector<int32_t>& 
 
 }  // namespace
 
+// Upper bound of the device memory one isomorphism query with result size k allocates on
+// graph G: its seeds (a whole label class at most) with their sort, its share of the batch
+// state, its result region and the final selection and merge over that region.
+int64_t iso_query_bytes(const nuri_graph* G, int32_t k) {
+  const int64_t seeds = std::max<int64_t>(G->d.n, 1);
+  const int64_t cap = std::max<int64_t>(16384, (int64_t)k * 64);
+  return seeds * (4 * 8 + 16) + (int64_t)NBINS * 4 + (int64_t)sizeof(IsoState) +
+         (int64_t)sizeof(IsoQuery) +
+         cap * ((int64_t)sizeof(IsoRes) + 4 + 8 + 4 * KCOLS + 4 * 4 + 8 * 2);
+}
+
 void topk_iso_batch(nuri_graph* G, int32_t nqueries, const nuri_query* qs, const int32_t* ks,
                     int32_t rank, uint32_t flags, cudaStream_t s, nuri_result** outs) {
   const DevGraph& g = G->d;
@@ -625,7 +647,8 @@ void topk_iso_batch(nuri_graph* G, int32_t nqueries, const nuri_query* qs, const
     int64_t c = seed_base[i + 1] - seed_base[i];
     if (c > 0) {
       ++launches;
-      k_iso_seeds<<<gridn(c), 256, 0, s>>>(cx, i, seed_base[i], c, prep[i].rootlab, keys.p, vals.p);
+      k_iso_seeds<<<gridn(c), 256, 0, s>>>(cx, i, seed_base[i], c, prep[i].rootlab,
+                                           G->part.index, G->part.count, keys.p, vals.p);
     }
   }
   if (nitems > 0) {
@@ -704,7 +727,30 @@ void topk_iso_batch(nuri_graph* G, int32_t nqueries, const nuri_query* qs, const
     cx.res_cap = d_cap.p;
     cx.work_next = work.p;
     NURI_CUDA(cudaEventRecord(ev0, s));
-    if (nitems > 0) {
+    if (nitems > 0 && G->part.count > 1 && G->part.exchange) {
+      // partitioned: the seeds in eight chunks (best bounds first), with the thresholds of
+      // all parts exchanged between chunks
+      const int64_t chunk = std::max<int64_t>((nitems + 7) / 8, 1 << 12);
+      for (int64_t off = 0; off < nitems; off += chunk) {
+        const int64_t cn = std::min(chunk, nitems - off);
+        NURI_CUDA(cudaMemsetAsync(work.p, 0, sizeof(unsigned long long), s));
+        ++launches;
+        k_iso_search<<<sm_count() * 4, ISO_WARPS * 32, 0, s>>>(cx, keys2.p + off, vals2.p + off, cn);
+        NURI_CUDA(cudaGetLastError());
+        NURI_CUDA(cudaMemcpyAsync(hs.data(), st.p, sizeof(IsoState) * nqueries,
+                                  cudaMemcpyDeviceToHost, s));
+        NURI_CUDA(cudaStreamSynchronize(s));
+        for (int i = 0; i < nqueries; ++i) {
+          if (!active[i]) continue;
+          const int64_t loc = hs[i].tau < 0 ? INT64_MIN : (int64_t)hs[i].tau;
+          const int64_t glob = G->part.exchange(G->part.ctx, i, loc);
+          if (glob > loc) {
+            ++launches;
+            k_iso_raise_tau<<<1, 32, 0, s>>>(st.p, i, (long long)glob);
+          }
+        }
+      }
+    } else if (nitems > 0) {
       ++launches;
       k_iso_search<<<sm_count() * 4, ISO_WARPS * 32, 0, s>>>(cx, keys2.p, vals2.p, nitems);
     }

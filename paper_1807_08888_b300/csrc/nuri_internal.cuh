@@ -116,6 +116,7 @@ struct DevGraph {
 
 struct nuri_graph {
   nuri::DevGraph d;
+  nuri_partition part{0, 1, nullptr, nullptr};  // seed partition of later queries
   int64_t num_edges = 0, dropped = 0;
   int32_t degeneracy = -1;  // from the peeling order (-1: degree order used)
   int32_t clique_split_bits = 0;  // dense-search task granularity chosen by nuri_tune_cliques
@@ -137,6 +138,17 @@ struct nuri_graph {
 
 namespace nuri {
 
+// The part of a seed vertex among `count` parts (MurmurHash3's 32-bit finaliser, mod count).
+__host__ __device__ __forceinline__ int32_t seed_part(int32_t v, int32_t count) {
+  uint32_t x = (uint32_t)v;
+  x ^= x >> 16;
+  x *= 0x85ebca6bu;
+  x ^= x >> 13;
+  x *= 0xc2b2ae35u;
+  x ^= x >> 16;
+  return count <= 1 ? 0 : (int32_t)(x % (uint32_t)count);
+}
+
 // graph_build.cu
 void build_graph(nuri_graph* g, int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
                  const uint8_t* labels, const int32_t* weights, int32_t index_hops,
@@ -149,7 +161,15 @@ nuri_result* new_result(int kind, int32_t count, int64_t nverts, int64_t nedges,
 void topk_cliques(nuri_graph* g, int32_t k, uint32_t flags, int64_t frontier_cap,
                   cudaStream_t s, nuri_result** out);
 
+// device bytes one clique query may allocate, and the local memory of the clique kernels
+int64_t clique_query_bytes(const nuri_graph* g, int32_t k, uint32_t flags, int64_t frontier_cap);
+int64_t clique_local_reserve_bytes();
+
+// server.cu: device bytes a request may hold while it runs
+int64_t request_bytes(const nuri_graph* g, const nuri_request& r);
+
 // iso.cu
+int64_t iso_query_bytes(const nuri_graph* g, int32_t k);
 void topk_iso_batch(nuri_graph* g, int32_t nq, const nuri_query* qs, const int32_t* ks,
                     int32_t rank, uint32_t flags, cudaStream_t s, nuri_result** outs);
 

@@ -2,12 +2,14 @@
 //
 // Requests (top-k cliques or top-k isomorphism) are submitted from any thread and return a
 // ticket.  `slots` worker threads each own a CUDA stream; a worker takes the oldest pending
-// request whose memory estimate fits the free part of the device-memory budget, and, when
-// the request is an isomorphism query, every other pending isomorphism query with the same
-// score mode (up to max_batch), which then run as one batched launch.  Requests that arrive
+// request whose memory estimate fits the free part of the device-memory budget, and every
+// other pending request of the same kind and settings (up to max_batch): isomorphism queries
+// with the same score mode then run as one batched launch, clique requests as one shared
+// search whose largest k answers all of them (nuri_topk_batch).  Requests that arrive
 // while others run are admitted as soon as a slot and memory free up, so the work of many
 // requests overlaps on the device (different streams).  Each request's result is the same as
 // when it runs alone: queries share only the read-only graph.
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -39,6 +41,7 @@ struct nuri_server {
     nuri_result* res;
     std::string err;
     double t_submit, t_start, t_done;
+    int64_t mem;
   };
   std::deque<Req> pending;
   std::map<uint64_t, Done> done;
@@ -46,9 +49,11 @@ struct nuri_server {
   std::vector<std::thread> workers;
   std::vector<cudaStream_t> streams;
   int64_t mem_in_use = 0;
+  int64_t fixed_bytes = 0;  // local memory of the clique kernels, reserved once per context
   uint64_t next_ticket = 1;
   bool stopping = false;
-  std::atomic<int64_t> n_batches{0}, n_batched{0};
+  std::atomic<int64_t> n_batches{0}, n_batched{0};              // isomorphism launches
+  std::atomic<int64_t> n_clique_batches{0}, n_clique_batched{0};  // shared clique searches
 };
 
 namespace nuri {
@@ -60,18 +65,18 @@ double now_ms() {
       .count();
 }
 
-// device memory a request may hold while it runs (result buffers, staging, scratch)
-int64_t estimate_mem(const nuri_graph* g, const nuri_request& r) {
-  if (r.kind == NURI_REQ_CLIQUES) {
-    int64_t rec = 520;  // bytes of one clique record
-    int64_t res = std::max<int64_t>(1 << 16, (int64_t)r.k * 64) * rec;
-    int64_t stage = std::max<int64_t>(1 << 16, (int64_t)g->d.max_out * 8) * rec;
-    int64_t scratch = g->d.max_out > 512 ? (int64_t)sm_count() * 24 * g->d.max_out * 4 : 0;
-    return res + 2 * stage + scratch + (int64_t)g->d.n * 24;
-  }
-  int64_t seeds = (int64_t)g->d.n * 32;
-  return seeds + (int64_t)std::max(4096, r.k * 8) * 40 + 16384 * 4;
+}  // namespace
+}  // namespace nuri
+
+// device memory a request may hold while it runs: the upper bound of every buffer its query
+// allocates (nuri_request_bytes)
+int64_t nuri::request_bytes(const nuri_graph* g, const nuri_request& r) {
+  if (r.kind == NURI_REQ_CLIQUES) return clique_query_bytes(g, r.k, r.flags, 0);
+  return iso_query_bytes(g, r.k);
 }
+
+namespace nuri {
+namespace {
 
 void worker_main(nuri_server* S, int slot) {
   cudaStream_t st = S->streams[slot];
@@ -84,20 +89,39 @@ void worker_main(nuri_server* S, int slot) {
       std::unique_lock<std::mutex> lk(S->mu);
       while (true) {
         if (S->stopping && S->pending.empty()) return;
-        // the oldest request that fits the free memory (first-come first-served otherwise)
+        // the oldest request that fits the free memory (first-come first-served otherwise);
+        // a request larger than the whole budget runs alone
         auto it = S->pending.begin();
         for (; it != S->pending.end(); ++it)
-          if (S->mem_in_use + it->mem <= S->cfg.mem_budget_bytes || S->mem_in_use == 0) break;
+          if (S->fixed_bytes + S->mem_in_use + it->mem <= S->cfg.mem_budget_bytes ||
+              S->mem_in_use == 0)
+            break;
         if (it != S->pending.end()) {
           batch.push_back(std::move(*it));
           S->pending.erase(it);
           mem = batch[0].mem;
+          if (batch[0].r.kind == NURI_REQ_CLIQUES) {
+            // clique requests with the same flags share one search (the largest k answers
+            // every smaller one): the group holds the memory of its largest request
+            for (auto jt = S->pending.begin();
+                 jt != S->pending.end() && (int)batch.size() < S->cfg.max_batch;) {
+              if (jt->r.kind == NURI_REQ_CLIQUES && jt->r.flags == batch[0].r.flags &&
+                  S->fixed_bytes + S->mem_in_use + std::max(mem, jt->mem) <=
+                      S->cfg.mem_budget_bytes) {
+                mem = std::max(mem, jt->mem);
+                batch.push_back(std::move(*jt));
+                jt = S->pending.erase(jt);
+              } else {
+                ++jt;
+              }
+            }
+          }
           if (batch[0].r.kind == NURI_REQ_ISO) {
             for (auto jt = S->pending.begin();
                  jt != S->pending.end() && (int)batch.size() < S->cfg.max_batch;) {
               if (jt->r.kind == NURI_REQ_ISO && jt->r.rank == batch[0].r.rank &&
                   jt->r.flags == batch[0].r.flags &&
-                  S->mem_in_use + mem + jt->mem <= S->cfg.mem_budget_bytes) {
+                  S->fixed_bytes + S->mem_in_use + mem + jt->mem <= S->cfg.mem_budget_bytes) {
                 mem += jt->mem;
                 batch.push_back(std::move(*jt));
                 jt = S->pending.erase(jt);
@@ -117,42 +141,41 @@ void worker_main(nuri_server* S, int slot) {
     std::vector<nuri_result*> res(batch.size(), nullptr);
     std::vector<std::string> err(batch.size());
     cudaSetDevice(dev);
-    if (batch[0].r.kind == NURI_REQ_CLIQUES) {
-      const nuri_request& r = batch[0].r;
-      status[0] = nuri_topk_cliques(S->g, r.k, r.rank, r.flags, 0, st, &res[0]);
-      if (status[0]) err[0] = nuri_last_error();
-    } else {
-      std::vector<nuri_query> qs(batch.size());
-      std::vector<int32_t> ks(batch.size());
+    {
+      // one nuri_topk_batch call: an isomorphism group is one batched launch, a clique group
+      // one shared search
+      std::vector<nuri_request> rq(batch.size());
       for (size_t i = 0; i < batch.size(); ++i) {
-        qs[i] = batch[i].r.query;
-        qs[i].labels = batch[i].qlab.data();
-        qs[i].src = batch[i].qsrc.data();
-        qs[i].dst = batch[i].qdst.data();
-        ks[i] = batch[i].r.k;
+        rq[i] = batch[i].r;
+        if (rq[i].kind == NURI_REQ_ISO) {
+          rq[i].query.labels = batch[i].qlab.data();
+          rq[i].query.src = batch[i].qsrc.data();
+          rq[i].query.dst = batch[i].qdst.data();
+        }
       }
-      nuri_status rc = nuri_topk_iso_batch(S->g, (int32_t)batch.size(), qs.data(), ks.data(),
-                                           batch[0].r.rank, batch[0].r.flags, st, res.data());
+      nuri_status rc = nuri_topk_batch(S->g, (int32_t)rq.size(), rq.data(), st, res.data());
       if (rc) {
         std::string e = nuri_last_error();
         for (size_t i = 0; i < batch.size(); ++i) {
           status[i] = rc;
           err[i] = e;
-          if (res[i]) {
-            nuri_free_result(res[i]);
-            res[i] = nullptr;
-          }
         }
       }
-      S->n_batches += 1;
-      S->n_batched += (int64_t)batch.size();
+      if (batch[0].r.kind == NURI_REQ_ISO) {
+        S->n_batches += 1;
+        S->n_batched += (int64_t)batch.size();
+      } else {
+        S->n_clique_batches += 1;
+        S->n_clique_batched += (int64_t)batch.size();
+      }
     }
     double t_done = now_ms();
     {
       std::lock_guard<std::mutex> lk(S->mu);
       S->mem_in_use -= mem;
       for (size_t i = 0; i < batch.size(); ++i)
-        S->done[batch[i].ticket] = {status[i], res[i], err[i], batch[i].t_submit, t_start, t_done};
+        S->done[batch[i].ticket] = {status[i], res[i],       err[i],       batch[i].t_submit,
+                                    t_start,   t_done,       batch[i].mem};
     }
     S->cv_done.notify_all();
     S->cv_work.notify_all();
@@ -176,7 +199,16 @@ nuri_status nuri_server_create(nuri_graph* g, const nuri_server_cfg* cfg, nuri_s
   S->g = g;
   S->cfg.slots = cfg && cfg->slots > 0 ? cfg->slots : 4;
   S->cfg.max_batch = cfg && cfg->max_batch > 0 ? cfg->max_batch : 64;
-  S->cfg.mem_budget_bytes = cfg && cfg->mem_budget_bytes > 0 ? cfg->mem_budget_bytes : (8ll << 30);
+  if (cfg && cfg->mem_budget_bytes > 0) {
+    S->cfg.mem_budget_bytes = cfg->mem_budget_bytes;
+  } else {  // default: 80 % of the device memory free now
+    size_t fr = 0, tot = 0;
+    S->cfg.mem_budget_bytes = cudaMemGetInfo(&fr, &tot) == cudaSuccess ? (int64_t)(fr * 0.8)
+                                                                      : (8ll << 30);
+  }
+  // the clique kernels' local memory is reserved by the driver once for the whole context
+  // (every stream shares it), so it is charged once against the budget, not per request
+  if (g->d.max_out > 64) S->fixed_bytes = clique_local_reserve_bytes();
   for (int i = 0; i < S->cfg.slots; ++i) {
     cudaStream_t st;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
@@ -236,7 +268,7 @@ nuri_status nuri_server_submit(nuri_server* S, const nuri_request* r, uint64_t* 
     q.qsrc.assign(qq.src, qq.src + qq.ne);
     q.qdst.assign(qq.dst, qq.dst + qq.ne);
   }
-  q.mem = estimate_mem(S->g, *r);
+  q.mem = request_bytes(S->g, *r);
   q.t_submit = now_ms();
   {
     std::lock_guard<std::mutex> lk(S->mu);
@@ -264,6 +296,9 @@ static nuri_status take_done(nuri_server* S, uint64_t ticket, nuri_result** out,
     times->queue_ms = d.t_start - d.t_submit;
     times->service_ms = d.t_done - d.t_start;
     times->total_ms = d.t_done - d.t_submit;
+    times->start_ms = d.t_start;
+    times->done_ms = d.t_done;
+    times->mem_bytes = d.mem;
   }
   if (d.status) set_error("%s", d.err.c_str());
   return d.status;
@@ -305,6 +340,36 @@ nuri_status nuri_server_stats(nuri_server* S, int64_t* batches, int64_t* batched
   if (!S) return NURI_ERR_INVALID;
   if (batches) *batches = S->n_batches.load();
   if (batched) *batched = S->n_batched.load();
+  return NURI_OK;
+}
+
+nuri_status nuri_server_clique_stats(nuri_server* S, int64_t* searches, int64_t* requests) {
+  if (!S) return NURI_ERR_INVALID;
+  if (searches) *searches = S->n_clique_batches.load();
+  if (requests) *requests = S->n_clique_batched.load();
+  return NURI_OK;
+}
+
+nuri_status nuri_server_budget(nuri_server* S, int64_t* budget_bytes, int64_t* fixed_bytes) {
+  if (!S) {
+    set_error("nuri_server_budget: NULL server");
+    return NURI_ERR_INVALID;
+  }
+  if (budget_bytes) *budget_bytes = S->cfg.mem_budget_bytes;
+  if (fixed_bytes) *fixed_bytes = S->fixed_bytes;
+  return NURI_OK;
+}
+
+nuri_status nuri_request_bytes(const nuri_graph* g, const nuri_request* r, int64_t* bytes) {
+  if (!g || !r || !bytes) {
+    set_error("nuri_request_bytes: NULL argument");
+    return NURI_ERR_INVALID;
+  }
+  if (r->k < 1 || (r->kind != NURI_REQ_CLIQUES && r->kind != NURI_REQ_ISO)) {
+    set_error("nuri_request_bytes: bad request kind or k");
+    return NURI_ERR_INVALID;
+  }
+  *bytes = request_bytes(g, *r);
   return NURI_OK;
 }
 

@@ -22,7 +22,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 __all__ = [
-    "Graph", "Query", "er_planted", "chung_lu_planted", "rmat", "labels_uniform",
+    "Graph", "Query", "er_planted", "chung_lu_planted", "expected_degrees", "rmat", "labels_uniform",
     "labels_zipf", "weights_uniform", "random_query", "query_batch", "er_small",
     "fixture_clique_example", "fixture_pattern_example", "path_query", "cycle_query",
     "star_query", "tree_query", "serving_requests", "workload",
@@ -135,21 +135,38 @@ def er_planted(n: int = 2000, p: float = 0.01, clique: int = 12, seed: int = 0) 
     return Graph(n, src, dst, planted=[c.tolist()], name=f"er{n}_p{p}_planted{clique}_s{seed}")
 
 
+def expected_degrees(n: int, mean_deg: float, beta: float) -> np.ndarray:
+    """Chung-Lu expected degrees: w_i proportional to (i+1)^(-1/(beta-1)), mean ``mean_deg``,
+    every weight at most sqrt(n * mean_deg).  Weights that pass the cap are pinned to it and
+    the rest are rescaled to keep the mean; this repeats until no free weight passes the cap."""
+    w = (np.arange(n, dtype=np.float64) + 1.0) ** (-1.0 / (beta - 1.0))
+    cap = np.sqrt(n * mean_deg)
+    clipped = np.zeros(n, dtype=bool)
+    for _ in range(64):
+        free = ~clipped
+        w[free] *= (mean_deg * n - cap * clipped.sum()) / w[free].sum()
+        over = free & (w > cap)
+        if not over.any():
+            break
+        w[over] = cap
+        clipped |= over
+    return w
+
+
 def chung_lu_planted(n: int = 1_000_000, mean_deg: float = 20.0, beta: float = 2.1,
                      n_cliques: int = 50, size_lo: int = 15, size_hi: int = 30,
                      seed: int = 0) -> Graph:
     """Chung-Lu power-law graph with vertex-disjoint planted cliques.
 
     Expected-degree weights w_i = (i+1)^(-1/(beta-1)) are scaled to mean ``mean_deg`` and
-    clipped at sqrt(n * mean_deg).  n*mean_deg/2 edges are drawn with both endpoints i.i.d.
+    clipped at sqrt(n * mean_deg): weights above the cap are set to it and only the unclipped
+    ones are rescaled, repeatedly, until the mean is ``mean_deg`` and no weight exceeds the
+    cap (``expected_degrees``).  n*mean_deg/2 edges are drawn with both endpoints i.i.d.
     proportional to w (inverse-CDF sampling), then the vertex ids are randomly permuted.
     Clique sizes are ``rng.integers(size_lo, size_hi + 1)``; members are disjoint, uniform.
     """
     rng = np.random.default_rng(seed)
-    w = (np.arange(n, dtype=np.float64) + 1.0) ** (-1.0 / (beta - 1.0))
-    w *= mean_deg * n / w.sum()
-    w = np.minimum(w, np.sqrt(n * mean_deg))
-    w *= mean_deg * n / w.sum()
+    w = expected_degrees(n, mean_deg, beta)
     cdf = np.cumsum(w)
     cdf /= cdf[-1]
     m = int(n * mean_deg / 2)

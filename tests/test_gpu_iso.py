@@ -175,3 +175,19 @@ def test_keep_ties_and_restart(monkeypatch):
     monkeypatch.delenv("NURI_RESULT_CAP")
     assert got.stats["restarts"] >= 1
     assert grows(got) == [tuple(r) for r in allr[:40]]
+
+
+@pytest.mark.parametrize("scale", [10, 12])
+def test_rmat_seven_and_eight_vertex_queries_k1000(scale):
+    """The largest query sizes of the workloads (7 and 8 vertices, every shape) with
+    k = 1000, in one batched launch and one at a time, against the oracle."""
+    g = _rmat_labelled(scale, 16, seed=40 + scale)
+    G = load(g)
+    rng = np.random.default_rng(scale)
+    qs = [synth.random_query(rng, kind, s, 8)
+          for kind in ("path", "cycle", "star", "tree") for s in (7, 8)]
+    batch = nuri.topk_iso_batch(G, qs, [1000] * len(qs))
+    for q, b in zip(qs, batch):
+        want = orows(g, q, 1000)
+        assert grows(b) == want, q
+        assert grows(nuri.topk_iso(G, q, 1000)) == want, q

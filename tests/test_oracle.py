@@ -343,3 +343,37 @@ def test_canonical_code_invariant_under_relabelling():
         edges2 = [(perm[a], perm[b]) for a, b in edges]
         code2, _ = oracle.canonical_code(labs2, edges2)
         assert code == code2 == brute.canon_code(nv, labs, edges)
+
+
+def test_iso_oracle_vs_brute_six_to_eight_vertex_queries():
+    """Algorithm 1 with the isomorphism functions, pinned by brute force at the query sizes
+    of the R-MAT workloads (6, 7 and 8 vertices, every shape), both score modes."""
+    rng = np.random.default_rng(29)
+    for i in range(8):
+        n = int(rng.integers(8, 12))
+        g = synth.er_small(n, [0.45, 0.6][i % 2], seed=900 + i)
+        g.labels = rng.integers(0, 2, size=n).astype(np.uint8)
+        g.weights = rng.integers(0, 30, size=n).astype(np.int32)
+        for kind in ("path", "cycle", "star", "tree"):
+            for s in (6, 7, 8):
+                q = synth.random_query(rng, kind, s, 2)
+                for k in (1, 10, 1000):
+                    for deg in (False, True):
+                        want = brute.topk_iso(g, q, k, deg)
+                        got = [r[:3] for r in oracle.topk_iso(g, q, k, deg)]
+                        assert got == want, (g.name, q, k, deg)
+
+
+def test_patterns_oracle_vs_brute_four_and_five_edges():
+    """Algorithm 2 with MNI support, pinned by brute force at M = 4 and M = 5 (patterns of up
+    to 6 vertices, the sizes of the R-MAT 18 workload) on 7-vertex graphs."""
+    rng = np.random.default_rng(31)
+    for i in range(6):
+        g = synth.er_small(7, [0.45, 0.6][i % 2], seed=950 + i)
+        g.labels = rng.integers(0, 2 + i % 2, size=7).astype(np.uint8)
+        for M in (4, 5):
+            for k in (1, 5, 50):
+                want = brute.topk_patterns(g, M, k)
+                got = oracle.topk_patterns(g, M, k)
+                got2 = [(r[0], brute.code_from_row(len(r[1]), r[3], r[2])) for r in got]
+                assert got2 == want, (g.name, M, k)

@@ -74,3 +74,18 @@ def test_query_batch_shapes():
                 seen.add(y)
                 todo.append(y)
         assert len(seen) == q.nq
+
+
+def test_chung_lu_expected_degrees_clipped_with_mean_kept():
+    # the stated recipe: mean expected degree 20, every weight at most sqrt(n * 20), the
+    # power law unchanged below the cap
+    n = 1_000_000
+    w = synth.expected_degrees(n, 20.0, 2.1)
+    cap = np.sqrt(n * 20.0)
+    assert w.max() <= cap * (1 + 1e-12)
+    assert abs(w.mean() - 20.0) < 1e-9
+    free = w < cap * (1 - 1e-12)
+    i = np.flatnonzero(free)[:1000]
+    ratio = w[i] / (i + 1.0) ** (-1.0 / 1.1)
+    assert np.allclose(ratio, ratio[0], rtol=1e-12)
+    assert 200 < np.count_nonzero(~free) < 1000
