@@ -51,8 +51,10 @@ def topk_cliques(g, k, maximal=False):
     return [(len(c), c) for c in cl[:k]]
 
 
-def iso_images(g, q, degree_rank=False):
-    """All distinct images (V_s, E_s) of non-induced matches, with their scores."""
+def iso_images(g, q, degree_rank=False, induced=False):
+    """All distinct images (V_s, E_s) of matches, with their scores: non-induced (query
+    edges land on data edges), or induced (also: non-adjacent query vertices land on
+    non-adjacent data vertices)."""
     adj = clean_adj(g)
     lab = g.labels.tolist()
     score = [len(adj[v]) for v in range(g.n)] if degree_rank else g.weights.tolist()
@@ -62,14 +64,19 @@ def iso_images(g, q, degree_rank=False):
         if len(set(mp)) != q.nq:
             continue
         if all(mp[b] in adj[mp[a]] for a, b in q.edges):
+            if induced:
+                qe = {(min(a, b), max(a, b)) for a, b in q.edges}
+                if any(mp[b] in adj[mp[a]] for a in range(q.nq) for b in range(a + 1, q.nq)
+                       if (a, b) not in qe):
+                    continue
             V = tuple(sorted(mp))
             E = tuple(sorted((min(mp[a], mp[b]), max(mp[a], mp[b])) for a, b in q.edges))
             images[(V, E)] = sum(score[v] for v in mp)
     return images
 
 
-def topk_iso(g, q, k, degree_rank=False):
-    im = iso_images(g, q, degree_rank)
+def topk_iso(g, q, k, degree_rank=False, induced=False):
+    im = iso_images(g, q, degree_rank, induced)
     rows = sorted(((s, V, E) for (V, E), s in im.items()), key=lambda r: (-r[0], r[1], r[2]))
     return rows[:k]
 

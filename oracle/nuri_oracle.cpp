@@ -543,11 +543,15 @@ extern "C" int orc_hop_index(int32_t n, int64_t m, const int32_t* src, const int
 //   one subgraph: an image already in R is not inserted again.
 // rank: 0 = weight sum, 1 = degree sum.  H_avail: number of index hops to use (>= query radius
 // is exact; hops beyond it use the per-label global maximum, which is also a valid bound).
+// induced != 0: the other reading of Section 2's definition (an edge between two images iff
+// there is one between the query vertices): expandable() also rejects an image adjacent to the
+// image of an already-matched query vertex that is not adjacent to the new one.
 // =============================================================================================
 extern "C" int orc_topk_iso(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
                             const uint8_t* labels, const int32_t* weights, int32_t rank,
                             int32_t nq, const uint8_t* qlab, int32_t qne, const int32_t* qsrc,
-                            const int32_t* qdst, int32_t k, int64_t budget, orc_result** out) {
+                            const int32_t* qdst, int32_t k, int64_t budget, int32_t induced,
+                            orc_result** out) {
   if (k < 1 || nq < 1 || nq > 8 || !labels) return 1;
   if (rank == 0 && !weights) return 1;
   double t0 = now_s();
@@ -703,6 +707,7 @@ extern "C" int orc_topk_iso(int32_t n, int64_t m, const int32_t* src, const int3
       for (int i = 0; i < s.depth && ok; ++i) {
         if (s.map[i] == x) ok = false;
         else if (qadj[q][order[i]] && !g.has(x, s.map[i])) ok = false;
+        else if (induced && !qadj[q][order[i]] && g.has(x, s.map[i])) ok = false;
       }
       if (!ok) continue;
       IsoSub c = s;

@@ -377,3 +377,24 @@ def test_patterns_oracle_vs_brute_four_and_five_edges():
                 got = oracle.topk_patterns(g, M, k)
                 got2 = [(r[0], brute.code_from_row(len(r[1]), r[3], r[2])) for r in got]
                 assert got2 == want, (g.name, M, k)
+
+
+def test_iso_oracle_induced_vs_brute():
+    """The induced reading (non-adjacent query vertices map to non-adjacent data vertices),
+    pinned by brute force; every induced match is also a non-induced one."""
+    rng = np.random.default_rng(37)
+    for g in _tiny_labelled(40, seed0=1300, nlab=2):
+        for q in _queries(rng, 2):
+            for k in (1, 5, 100):
+                for deg in (False, True):
+                    want = brute.topk_iso(g, q, k, deg, induced=True)
+                    got = [r[:3] for r in oracle.topk_iso(g, q, k, deg, induced=True)]
+                    assert got == want, (g.name, q, k, deg)
+                    every = {r[1:3] for r in brute.topk_iso(g, q, 10 ** 9, deg)}
+                    assert all(r[1:3] in every for r in got)
+    # a path a-b-c inside a triangle is a non-induced match but not an induced one
+    g = synth.Graph(3, np.array([0, 1, 0], np.int32), np.array([1, 2, 2], np.int32),
+                    labels=np.zeros(3, np.uint8), weights=np.ones(3, np.int32))
+    q = synth.path_query([0, 0, 0])
+    assert len(oracle.topk_iso(g, q, 10)) == 3
+    assert len(oracle.topk_iso(g, q, 10, induced=True)) == 0
