@@ -106,6 +106,63 @@ class Clocks:
                 "samples": len(self.rows)}
 
 
+def source_digest():
+    """SHA-256 (16 hex) of the clique engine's source: DRAM counters taken on another
+    version of the kernels no longer describe them."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("cliques.cu", "nuri_internal.cuh", "topk_common.cuh"):
+        with open(os.path.join(ROOT, "paper_1807_08888_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def rooflines(total_ms, csr_bytes, csr_ms, csr_launches, tail_words, tail_ms, tail_launches):
+    """HBM rooflines of the two clique kernels, dominant (larger share of the step) first,
+    then the task kernel's bit-operation rate against a derived ALU peak.
+
+    Algorithmic bytes per unit of work: a CSR expansion reads 4 B per adjacency entry it
+    intersects (the kernel counts them, stats adj_bytes); a bitmap-tail node combines 64-bit
+    row words into candidate masks, 8 B per word (stats tail_words).  achieved = those bytes
+    per launch / the launch's CUDA-event time; traffic = DRAM bytes per launch, from the ncu
+    capture in profiles/traffic.json (DRAM bytes per algorithmic byte on the 200k-vertex case,
+    times this launch's algorithmic bytes), or null when the kernels changed since."""
+    peak, peak_kind = peaks()
+    traffic = {}
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            traffic = json.load(f)
+    except Exception:
+        pass
+    digest = source_digest()
+
+    def line(kernel, key, alg_bytes, ms, launches):
+        ms = max(ms, 1e-9)
+        per_launch = alg_bytes / max(launches, 1)
+        achieved = alg_bytes / (ms / 1e3) / 1e9
+        t = traffic.get(key) or {}
+        tr = (t["dram_per_algorithmic_byte"] * per_launch
+              if t.get("source_digest") == digest and t.get("dram_per_algorithmic_byte")
+              else None)
+        return {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json), of {peak_kind}",
+                "traffic": tr, "algorithmic_bytes_per_launch": per_launch,
+                "avg_launch_ms": ms / max(launches, 1), "launches": launches,
+                "share_of_step": ms / total_ms,
+                "traffic_source": t.get("source") if tr is not None else
+                "no capture of this kernel version"}
+
+    csr = line("k_clique_expand", "k_clique_expand", csr_bytes, csr_ms, csr_launches)
+    tail = line("k_clique_tasks", "k_clique_tasks", 8.0 * tail_words, tail_ms, tail_launches)
+    apeak = alu_peak_gops()
+    tach = (tail_words / (tail_ms / 1e3)) / 1e9 if tail_ms > 0 else 0.0
+    alu = {"bound": "alu", "kernel": "k_clique_tasks", "achieved": tach, "peak": apeak,
+           "unit": "Gword-ops/s", "frac": tach / apeak,
+           "peak_source": "derived: 148 SMs x 32 64-bit logical ops/clk x sm_max_mhz"}
+    return (csr, tail, alu) if csr_ms >= tail_ms else (tail, csr, alu)
+
+
 def combine_ranks(total_ms, total_units, dist=None, device="cpu"):
     """Whole-job aggregate over replicas: the slowest rank's time and the units of all ranks
     (value = units / time).  Works with any torch.distributed backend (gloo on CPU in tests,
@@ -256,37 +313,9 @@ def main():
     if dist:
         total_ms, total_exp = combine_ranks(total_ms, total_exp, dist, device="cuda")
     value = total_exp / (total_ms / 1e3)
-    peak, peak_kind = peaks()
-    # CSR expansion (k_clique_expand over frontier records and seeds): adjacency bytes over
-    # its own event-timed launches
-    csr_ms = max(sum(exp_ms), 1e-9)
-    achieved = (sum(exp_bytes) / (csr_ms / 1e3)) / 1e9
-    traffic = {}
-    try:
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            traffic = json.load(f)
-    except Exception:
-        pass
-    roof_csr = {"bound": "hbm", "kernel": "k_clique_expand", "achieved": achieved,
-                "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
-                "traffic": traffic.get("k_clique_expand_chunglu1m"),
-                "algorithmic_bytes_per_launch": sum(exp_bytes) / max(exp_launches, 1),
-                "avg_launch_ms": csr_ms / max(exp_launches, 1), "share_of_step":
-                csr_ms / total_ms}
-    apeak = alu_peak_gops()
-    tach = (tail_words / (tail_ms / 1e3)) / 1e9 if tail_ms > 0 else 0.0
-    roof_tail = {"bound": "alu", "kernel": "k_clique_tasks<8>", "achieved": tach,
-                 "peak": apeak, "unit": "Gword-ops/s", "frac": tach / apeak,
-                 "peak_source": "derived: 148 SMs x 32 64-bit logical ops/clk x sm_max_mhz",
-                 # DRAM bytes of one captured wave (ncu); its duration beside it
-                 "traffic": (traffic.get("k_clique_tasks_chunglu1m") or {}).get("dram_bytes"),
-                 "traffic_launch_ms": (traffic.get("k_clique_tasks_chunglu1m") or {}).get(
-                     "launch_ms"),
-                 "algorithmic_words_per_launch": tail_words / max(tail_launches, 1),
-                 "avg_launch_ms": tail_ms / max(tail_launches, 1),
-                 "share_of_step": tail_ms / total_ms}
-    dominant, secondary = ((roof_tail, roof_csr) if tail_ms > csr_ms else (roof_csr, roof_tail))
+    roofs = rooflines(total_ms, sum(exp_bytes), sum(exp_ms), exp_launches,
+                      tail_words, tail_ms, tail_launches)
+    dominant, secondary = roofs[0], roofs[1]
     last = r
     line = {
         "metric": METRIC, "value": value, "unit": "expansions/s", "n_gpus": world,
@@ -304,7 +333,7 @@ def main():
         "expansions_per_step": total_exp / args.steps / world,
         "threshold": last.stats["threshold"], "rounds_per_step": last.stats["rounds"],
         "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
-        "roofline": dominant, "roofline_secondary": secondary,
+        "roofline": dominant, "roofline_secondary": secondary, "roofline_alu": roofs[2],
         "clocks": clk.summary(),
     }
     # end to end through the public API with host buffers: H2D of the edge list, graph build,
@@ -330,7 +359,7 @@ def main():
                    "d2h_bytes_per_step": int(d2h),
                    "includes": "H2D edge list, device CSR build, query, D2H rows"}
     if not args.no_extra and rank == 0:
-        line["workloads"] = extra_workloads(nuri, torch, sptr)
+        line["workloads"] = extra_workloads(nuri, torch, sptr, G)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.ref_budget)
     if rank == 0:
@@ -468,11 +497,47 @@ def serving(args, nuri, torch, sptr):
     return out
 
 
-def extra_workloads(nuri, torch, sptr):
-    """The other configurations: ER planted clique, the 64-query isomorphism batch (batched
-    launch vs one query at a time), and pattern mining M = 1..5."""
+def clique_batch_vs_plain(nuri, torch, G, sptr, count=16, seed=5):
+    """Top-k clique requests (k uniform 1..100) on one graph: one nuri_topk_batch call (one
+    shared search for the largest k) against the plain path (one nuri_topk_cliques call per
+    request), each timed with CUDA events on the query stream."""
+    rng = np.random.default_rng(seed)
+    ks = [int(x) for x in rng.integers(1, 101, size=count)]
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1)
+
+    timed(lambda: nuri.topk_batch(G, [("clique", k) for k in ks], stream=sptr))  # warm-up
+    batch, bms = timed(lambda: nuri.topk_batch(G, [("clique", k) for k in ks], stream=sptr))
+    plain_ms, plain_exp, same = 0.0, 0, True
+    for k, b in zip(ks, batch):
+        r, ms = timed(lambda: nuri.topk_cliques(G, k, stream=sptr))
+        plain_ms += ms
+        plain_exp += r.stats["expansions"]
+        same &= [tuple(x) for x in r] == [tuple(x) for x in b]
+    return {"requests": count, "ks": ks, "batched_time_to_topk_ms": bms,
+            "plain_time_to_topk_ms": plain_ms, "batched_speedup": plain_ms / bms,
+            "batched_expansions": batch[0].stats["expansions"], "plain_expansions": plain_exp,
+            "batched_expansions_per_s": batch[0].stats["expansions"] / (bms / 1e3),
+            "plain_expansions_per_s": plain_exp / (plain_ms / 1e3),
+            "rows_equal_plain": bool(same)}
+
+
+def extra_workloads(nuri, torch, sptr, G_headline=None):
+    """The other configurations: clique requests batched vs one at a time on the headline
+    graph, ER planted clique, the 64-query isomorphism batch (batched launch vs one query at a
+    time), and pattern mining M = 1..5."""
     import synth
     out = {}
+    if G_headline is not None:
+        out["chunglu1m_clique_batch16"] = clique_batch_vs_plain(nuri, torch, G_headline, sptr)
     g = synth.workload("er2000")
     G = nuri.load_graph(g.n, g.src, g.dst, stream=sptr)
     for _ in range(3):

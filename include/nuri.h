@@ -64,6 +64,10 @@ typedef int32_t nuri_status;
 /* flags common to all queries */
 #define NURI_KEEP_TIES 0x100u       /* return every row tied with the k-th (|R| may exceed k) */
 #define NURI_NO_PRUNE 0x200u        /* disable pruning and prioritization (Nuri-NP ablation)  */
+/* nuri_topk_iso flags */
+#define NURI_ISO_INDUCED 0x400u     /* induced matches: non-adjacent query vertices map to
+                                       non-adjacent data vertices (Section 2's isomorphism
+                                       definition read as "edge if and only if edge")       */
 
 typedef struct nuri_graph nuri_graph;
 
@@ -173,6 +177,7 @@ nuri_status nuri_topk_cliques(nuri_graph* g, int32_t k, int32_t rank, uint32_t f
  * image subgraphs; Section 4.3 functions: score = sum of vertex scores, upper bound =
  * score + sum over unmatched query vertices of index(root image, label, hop)).
  *   rank   NURI_RANK_WEIGHT_SUM or NURI_RANK_DEGREE_SUM
+ *   flags  NURI_KEEP_TIES, NURI_ISO_INDUCED (induced matches only)
  * Errors: NURI_ERR_INVALID (nq outside 1..8, disconnected query, no labels/weights).
  */
 nuri_status nuri_topk_iso(nuri_graph* g, const nuri_query* q, int32_t k, int32_t rank,

@@ -33,7 +33,7 @@ REQ_CLIQUES, REQ_ISO, REQ_PATTERNS = 0, 1, 2
 RANK_SIZE, RANK_WEIGHT_SUM, RANK_DEGREE_SUM, RANK_MNI = range(4)
 LOAD_DEVICE_INPUT, LOAD_NO_ISO = 0x1, 0x2
 CLIQUE_ALL, CLIQUE_MAXIMAL = 0x0, 0x1
-KEEP_TIES, NO_PRUNE = 0x100, 0x200
+KEEP_TIES, NO_PRUNE, ISO_INDUCED = 0x100, 0x200, 0x400
 
 # every function include/nuri.h declares
 EXPORTS = (
@@ -325,19 +325,20 @@ def _query_struct(q, keep):
     return _Query(int(q.nq), int(s.size), lab.ctypes.data, s.ctypes.data, d.ctypes.data)
 
 
-def topk_iso(g: Graph, q, k: int, degree_rank=False, keep_ties=False, stream=None) -> Result:
-    return topk_iso_batch(g, [q], [k], degree_rank, keep_ties, stream)[0]
+def topk_iso(g: Graph, q, k: int, degree_rank=False, keep_ties=False, stream=None,
+             induced=False) -> Result:
+    return topk_iso_batch(g, [q], [k], degree_rank, keep_ties, stream, induced)[0]
 
 
 def topk_iso_batch(g: Graph, queries, ks, degree_rank=False, keep_ties=False,
-                   stream=None) -> list:
+                   stream=None, induced=False) -> list:
     keep = []
     nq = len(queries)
     arr = (_Query * nq)(*[_query_struct(q, keep) for q in queries])
     kk = np.ascontiguousarray(ks, dtype=np.int32)
     outs = (ctypes.POINTER(_Result) * nq)()
     rank = RANK_DEGREE_SUM if degree_rank else RANK_WEIGHT_SUM
-    flags = KEEP_TIES if keep_ties else 0
+    flags = (KEEP_TIES if keep_ties else 0) | (ISO_INDUCED if induced else 0)
     _check(lib().nuri_topk_iso_batch(g.handle, nq, arr, kk.ctypes.data_as(ctypes.c_void_p),
                                      rank, flags, _stream(stream), outs))
     return [_unpack(outs[i]) for i in range(nq)]

@@ -6,6 +6,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <mutex>
 #include <new>
 #include <utility>
 #include <vector>
@@ -31,6 +32,32 @@ uint64_t time_budget_ns() { return g_budget_ns.load(); }
 __global__ void k_set_deadline(uint64_t* deadline, uint64_t budget_ns) {
   if (threadIdx.x == 0 && blockIdx.x == 0)
     *deadline = budget_ns ? global_ns() + budget_ns : ~0ull;
+}
+
+// One pool per device, created on first use.  Its release threshold keeps up to
+// NURI_POOL_KEEP_MB (default 8192) MB of freed memory cached between synchronisations.
+cudaMemPool_t device_pool() {
+  static std::mutex mu;
+  static std::vector<cudaMemPool_t> pools;
+  int dev = 0;
+  NURI_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  if ((int)pools.size() <= dev) pools.resize(dev + 1, nullptr);
+  if (!pools[dev]) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool;
+    NURI_CUDA(cudaMemPoolCreate(&pool, &props));
+    uint64_t keep = 8192ull << 20;
+    if (const char* e = getenv("NURI_POOL_KEEP_MB")) keep = (uint64_t)atoll(e) << 20;
+    NURI_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    pools[dev] = pool;
+  }
+  return pools[dev];
 }
 
 nuri_result* new_result(int kind, int32_t count, int64_t nverts, int64_t nedges, bool labels) {

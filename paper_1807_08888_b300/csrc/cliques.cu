@@ -980,13 +980,37 @@ __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
         const int32_t t_now = ld_volatile(&cx.st->tau);
         if (t_now != INT32_MIN && t_now - nv > 1) core_need = t_now - nv;
       }
+      // candidates inside the core bitmap (the last ranks of the order): rows come from bit
+      // tests of the bitmap, every (candidate, 32 candidates) step independent of the others
+      const bool in_core = g.core_bits != nullptr && sp[0] >= g.core_base;
       int pass = 0;
       for (; pass < 2; ++pass) {
         if (pass == 1) {
           for (int i = lane; i < p * W; i += 32) rows[i] = 0;
           __syncwarp();
         }
-        for (int i = 0; i < p; ++i) {
+        if (in_core) {
+          const int cw = g.core_n >> 6;
+          const int nch = (p + 31) >> 5;
+          for (int t = 0; t < p * nch; ++t) {
+            const int i = t / nch, j = ((t - i * nch) << 5) + lane;
+            bool hit = false;
+            if (j < p && j != i) {
+              const int x = sp[j] - g.core_base;
+              hit = (__ldg(g.core_bits + (int64_t)(sp[i] - g.core_base) * cw + (x >> 6)) >>
+                     (x & 63)) & 1ull;
+            }
+            if (pass == 0) {
+              const unsigned b = __ballot_sync(FULL, hit);
+              if (lane == 0 && b) dg[i] += __popc(b);
+            } else if (hit) {
+              const int a = inv[i], c = inv[j];
+              atomicOr(rows + a * W + (c >> 6), 1ull << (c & 63));
+            }
+          }
+          if (lane == 0) my_bytes += 4ull * (unsigned long long)p * nch;
+        }
+        for (int i = 0; i < p && !in_core; ++i) {
           int32_t v = sp[i];
           int64_t rb = g.ooff[v], re = g.ooff[v + 1];
           int64_t scanned = 0;
@@ -1650,7 +1674,7 @@ __global__ void k_select(const Rec* res, int64_t cnt, int32_t tau, const DevGrap
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt;
        i += (int64_t)gridDim.x * blockDim.x) {
     int c = res[i].nv;
-    if (c < tau) continue;
+    if (c < tau || c > MAXD) continue;  // rows are cliques of 1..MAXD vertices
     int pos = atomicAdd(nsel, 1);
     int32_t ids[MAXD];
     for (int t = 0; t < c; ++t) ids[t] = __ldg(g.vert_of + res[i].V[t]);
@@ -2272,7 +2296,7 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
     NURI_CUDA(cudaMemcpyAsync(gtau.p, &neg, 4, cudaMemcpyHostToDevice, s));
     const int64_t c0 = seed_lo[NB - 1], n0 = seed_lo[0] - c0;  // class 0 (wide) seeds
     const int64_t n1 = seed_hi[NB];                             // class 1 (narrow) seeds
-    const int64_t take0 = std::min<int64_t>(n0, 4096), take1 = std::min<int64_t>(n1, 16384);
+    const int64_t take0 = std::min<int64_t>(n0, 4096), take1 = std::min<int64_t>(n1, 65536);
     if (take0 > 0) {
       ++launches;
       k_greedy_tau<<<gblocks, 256, 0, s>>>(g, svals2.p + c0, take0, k, gbuf.p, gtau.p);
@@ -2564,6 +2588,10 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
       }
       NURI_CUDA(cudaStreamSynchronize(s));
     }
+    // the state read at the top of the last round predates that round's result compaction
+    // (which lowers res_count): read it again before the rows are selected
+    NURI_CUDA(cudaMemcpyAsync(&hs, st.p, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    NURI_CUDA(cudaStreamSynchronize(s));
     // drop what is left (every remaining bound < tau)
     for (auto& b : buckets) {
       for (Rec* p : b.spilled) cudaFreeHost(p);

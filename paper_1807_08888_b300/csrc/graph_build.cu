@@ -136,6 +136,124 @@ __global__ void k_peel_remove(const int64_t* __restrict__ off, const int32_t* __
   }
 }
 
+// The unassigned vertices (batch < 0), compacted into list (order not kept).
+__global__ void k_peel_list(const int32_t* __restrict__ batch, int32_t n,
+                            int32_t* __restrict__ list, int32_t* cnt) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    if (batch[v] < 0) list[atomicAdd(cnt, 1)] = (int32_t)v;
+}
+
+// The rest of the peel in one CTA, once few vertices remain (the long tail of small batches
+// would otherwise cost a launch and a host round trip each).  Same rule as the batch loop on
+// the host: when the front is empty, k rises to the smallest remaining degree and every
+// unassigned vertex with remaining degree <= k forms batch b; removing a batch lowers its
+// neighbours' degrees and those that drop to <= k form batch b + 1.  list/nlist: the
+// unassigned vertices (la, lb: two buffers of that size); fa, fb: fronts (same size);
+// front/nfront: the current front (batch b), k, b: the current level and batch.
+// out[0] = the largest k reached, out[1] = 0 on success, 1 if a front came out empty while
+// vertices remained (cannot happen; reported instead of looping).
+__global__ void __launch_bounds__(1024) k_peel_tail(
+    const int64_t* __restrict__ off, const int32_t* __restrict__ adj, int32_t* __restrict__ rem,
+    int32_t* __restrict__ batch, int32_t* la, int32_t* lb, int32_t nlist, int32_t* fa,
+    int32_t* fb, int32_t nfront0, int32_t k0, int32_t b0, int32_t* out) {
+  __shared__ int32_t s_nlist, s_nfront, s_nnext, s_k, s_min, s_cnt;
+  __shared__ int64_t s_remaining;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
+  int32_t* list = la;
+  int32_t* list2 = lb;
+  int32_t* front = fa;
+  int32_t* next = fb;
+  int32_t b = b0;
+  if (tid == 0) {
+    s_nlist = nlist;
+    s_nfront = nfront0;
+    s_nnext = 0;
+    s_k = k0;
+    s_remaining = nlist;  // the current front is still in the list (batch >= 0 there)
+  }
+  __syncthreads();
+  // the list holds the front too: count the unassigned part
+  if (tid == 0) s_cnt = 0;
+  __syncthreads();
+  for (int i = tid; i < s_nlist; i += nthr)
+    if (batch[list[i]] < 0) atomicAdd(&s_cnt, 1);
+  __syncthreads();
+  if (tid == 0) s_remaining = (int64_t)s_cnt + s_nfront;
+  __syncthreads();
+  while (s_remaining > 0) {
+    if (s_nfront == 0) {
+      // compact the list to the unassigned vertices, take their smallest remaining degree
+      if (tid == 0) {
+        s_cnt = 0;
+        s_min = INT32_MAX;
+      }
+      __syncthreads();
+      const int32_t nl = s_nlist;
+      for (int i = tid; i < nl; i += nthr) {
+        const int32_t v = list[i];
+        if (batch[v] < 0) {
+          list2[atomicAdd(&s_cnt, 1)] = v;
+          atomicMin(&s_min, rem[v]);
+        }
+      }
+      __syncthreads();
+      {
+        int32_t* t = list;
+        list = list2;
+        list2 = t;
+      }
+      if (tid == 0) {
+        s_nlist = s_cnt;
+        s_k = max(s_k, s_min);
+        s_nfront = 0;
+      }
+      __syncthreads();
+      const int32_t k = s_k;
+      for (int i = tid; i < s_nlist; i += nthr) {
+        const int32_t v = list[i];
+        if (rem[v] <= k) {
+          batch[v] = b;
+          front[atomicAdd(&s_nfront, 1)] = v;
+        }
+      }
+      __syncthreads();
+      if (s_nfront == 0) {
+        if (tid == 0) out[1] = 1;
+        return;
+      }
+    }
+    const int32_t k = s_k, nf = s_nfront;
+    for (int w = warp; w < nf; w += nwarps) {
+      const int32_t v = front[w];
+      for (int64_t t = off[v] + lane; t < off[v + 1]; t += 32) {
+        const int32_t u = adj[t];
+        if (*(volatile int32_t*)(batch + u) >= 0) continue;
+        const int32_t old = atomicSub(rem + u, 1);
+        if (old - 1 <= k && atomicCAS(batch + u, -1, b + 1) == -1) next[atomicAdd(&s_nnext, 1)] = u;
+      }
+    }
+    __syncthreads();
+    {
+      int32_t* t = front;
+      front = next;
+      next = t;
+    }
+    if (tid == 0) {
+      s_remaining -= nf;
+      s_nfront = s_nnext;
+      s_nnext = 0;
+    }
+    ++b;
+    __syncthreads();
+  }
+  if (tid == 0) {
+    out[0] = s_k;
+    out[1] = 0;
+  }
+}
+
 __global__ void k_peel_keys(const int32_t* __restrict__ batch, int32_t n,
                             uint64_t* __restrict__ keys) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
@@ -467,6 +585,7 @@ void build_label_segments(const DevGraph& d, const uint64_t* ckeys, const int32_
 // kMaxPeelBatches batches (then the caller uses the degree order).
 static bool peel_order(nuri_graph* g, uint64_t* keys, cudaStream_t s) {
   constexpr int kMaxPeelBatches = 20000;
+  constexpr int64_t kTailVertices = 1 << 16;  // at most this many left: one-CTA tail kernel
   const int32_t n = g->d.n;
   DBuf<int32_t> rem, batch, fa, fb, cnt;
   rem.alloc(n, s);
@@ -482,6 +601,29 @@ static bool peel_order(nuri_graph* g, uint64_t* keys, cudaStream_t s) {
   int32_t maxk = 0;
   while (remaining > 0) {
     if (b > kMaxPeelBatches) return false;
+    if (remaining <= kTailVertices) {
+      // finish on the device in one CTA
+      DBuf<int32_t> la, lb, tout;
+      la.alloc(remaining, s);
+      lb.alloc(remaining, s);
+      tout.alloc(2, s);
+      NURI_CUDA(cudaMemsetAsync(cnt.p, 0, 4, s));
+      k_peel_list<<<blocks_for(n), kThreads, 0, s>>>(batch.p, n, la.p, cnt.p);
+      int32_t nl = 0;
+      NURI_CUDA(cudaMemcpyAsync(&nl, cnt.p, 4, cudaMemcpyDeviceToHost, s));
+      NURI_CUDA(cudaStreamSynchronize(s));
+      // fronts need room for every remaining vertex; fa/fb hold n entries
+      k_peel_tail<<<1, 1024, 0, s>>>(g->off.p, g->adj.p, rem.p, batch.p, la.p, lb.p, nl, front,
+                                     next, nfront, k, b, tout.p);
+      NURI_CUDA(cudaGetLastError());
+      int32_t to[2] = {0, 1};
+      NURI_CUDA(cudaMemcpyAsync(to, tout.p, 8, cudaMemcpyDeviceToHost, s));
+      NURI_CUDA(cudaStreamSynchronize(s));
+      if (to[1] != 0) return false;
+      maxk = std::max(maxk, to[0]);
+      remaining = 0;
+      break;
+    }
     if (nfront == 0) {
       int32_t init = INT32_MAX;
       NURI_CUDA(cudaMemcpyAsync(cnt.p, &init, 4, cudaMemcpyHostToDevice, s));
@@ -511,6 +653,24 @@ static bool peel_order(nuri_graph* g, uint64_t* keys, cudaStream_t s) {
   g->degeneracy = maxk;
   k_peel_keys<<<blocks_for(n), kThreads, 0, s>>>(batch.p, n, keys);
   return true;
+}
+
+// The core bitmap: one warp per core rank r scans r's out-row (ranks above r, all in the
+// core) and sets both directions of every edge.
+constexpr int32_t kCoreRanks = 4096;
+__global__ void k_core_bits(const int64_t* __restrict__ ooff, const int32_t* __restrict__ oout,
+                            int32_t base, int32_t cn, unsigned long long* __restrict__ bits) {
+  const int lane = threadIdx.x & 31;
+  const int32_t words = cn / 64;
+  for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < cn;
+       w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int32_t r = base + (int32_t)w;
+    for (int64_t t = ooff[r] + lane; t < ooff[r + 1]; t += 32) {
+      const int32_t x = oout[t] - base;
+      atomicOr(&bits[w * words + (x >> 6)], 1ull << (x & 63));
+      atomicOr(&bits[(int64_t)x * words + (w >> 6)], 1ull << (w & 63));
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -657,6 +817,18 @@ void build_graph(nuri_graph* g, int32_t n, int64_t m, const int32_t* src, const 
   d.oout = g->oout.p;
   d.vert_of = g->vert_of.p;
   d.rank_of = g->rank_of.p;
+  // core bitmap of the last ranks (multiple of 64 wide, at most kCoreRanks)
+  if (n >= 64 && d.max_out > 64) {
+    const int32_t cn = std::min<int32_t>(kCoreRanks, n & ~63);
+    g->core_bits.alloc((int64_t)cn * (cn / 64), s);
+    NURI_CUDA(cudaMemsetAsync(g->core_bits.p, 0, g->core_bits.bytes(), s));
+    k_core_bits<<<std::max(1, std::min(cn / 8, sm_count() * 16)), 256, 0, s>>>(
+        g->ooff.p, g->oout.p, n - cn, cn, g->core_bits.p);
+    NURI_CUDA(cudaGetLastError());
+    d.core_base = n - cn;
+    d.core_n = cn;
+    d.core_bits = g->core_bits.p;
+  }
 
   // 4. labels, weights, label segments, hop index
   if (weights) {

@@ -56,12 +56,14 @@ struct IsoQuery {
   int32_t hop[QMAX];     // hop (query distance from the root) of position i
   int32_t lab[QMAX];     // label of position i
   uint32_t back[QMAX];   // earlier positions adjacent to position i, parent excluded
+  uint32_t nonadj[QMAX]; // induced matching: earlier positions NOT adjacent to position i
   uint32_t sym_lt[QMAX]; // earlier positions a that must satisfy mu(a) < mu(i)
   uint32_t sym_gt[QMAX]; // earlier positions a that must satisfy mu(a) > mu(i)
   int32_t ne;
   int32_t epos[EMAX][2]; // query edges as position pairs
   int32_t shift;         // histogram bin = score >> shift
-  int32_t pad;
+  int32_t refine;        // bound each unmatched position by its nearest matched one
+  int8_t qd[QMAX][QMAX]; // query distance between positions
 };
 
 struct IsoState {
@@ -316,6 +318,13 @@ __global__ void __launch_bounds__(ISO_WARPS * 32) k_iso_search(IsoCtx cx,
             m &= m - 1;
             valid = row_contains(g, mu[a], c.x);
           }
+          // induced matching: no data edge where the query has none
+          m = Q.nonadj[lev];
+          while (m && valid) {
+            int a = __ffs(m) - 1;
+            m &= m - 1;
+            valid = !row_contains(g, mu[a], c.x);
+          }
         }
         unsigned inm = __ballot_sync(FULL, in);
         unsigned okm = __ballot_sync(FULL, okb);
@@ -350,6 +359,20 @@ __global__ void __launch_bounds__(ISO_WARPS * 32) k_iso_search(IsoCtx cx,
       mu[lev] = c.x;
       sc[lev + 1] = s_new;
       ++lev;
+      if (Q.refine && lev + 1 < nq) {
+        // rest[lev] = sum over the positions after lev of the smallest index bound any
+        // matched position gives (each is a valid bound: the image lies within the query
+        // distance, as a walk, of that matched image); lane p computes position p
+        long long term = 0;
+        if (lane > lev && lane < nq) {
+          long long best = LLONG_MAX;
+          for (int a = 0; a < lev; ++a)
+            best = min(best, index_value(cx, mu[a], Q.qd[a][lane], Q.lab[lane]));
+          term = best < 0 ? NONE : best;
+        }
+        for (int o = 16; o; o >>= 1) term += __shfl_xor_sync(FULL, term, o);
+        rest[lev] = term < 0 ? NONE : term;  // matched position 0 is in the min: <= root bound
+      }
       int32_t a = mu[Q.ppos[lev]];
       int64_t so = (int64_t)a * g.L + Q.lab[lev];
       pos[lev] = g.lsoff[so];
@@ -458,7 +481,7 @@ struct Prepared {
 };
 
 bool prepare_query(const nuri_query& in, int32_t k, const std::vector<int32_t>& gmax, int L,
-                   Prepared* out) {
+                   bool induced, Prepared* out) {
   int nq = in.nq;
   int A[QMAX][QMAX] = {};
   for (int e = 0; e < in.ne; ++e) {
@@ -511,10 +534,13 @@ bool prepare_query(const nuri_query& in, int32_t k, const std::vector<int32_t>& 
     Q.hop[i] = dist[qv];
     Q.lab[i] = in.labels[qv];
     Q.ppos[i] = i == 0 ? -1 : posof[par[qv]];
-    uint32_t bk = 0;
-    for (int j = 0; j < i; ++j)
+    uint32_t bk = 0, na = 0;
+    for (int j = 0; j < i; ++j) {
       if (A[qv][order[j]] && j != Q.ppos[i]) bk |= 1u << j;
+      if (!A[qv][order[j]]) na |= 1u << j;
+    }
     Q.back[i] = bk;
+    Q.nonadj[i] = induced ? na : 0u;
   }
   Q.ne = 0;
   for (int a = 0; a < nq; ++a)
@@ -574,6 +600,18 @@ bool prepare_query(const nuri_query& in, int32_t k, const std::vector<int32_t>& 
       if (s[pick] == pick) stab.push_back(s);
     aut.swap(stab);
   }
+  // query distances between positions (Floyd-Warshall on <= 8 vertices)
+  {
+    int D[QMAX][QMAX];
+    for (int a = 0; a < nq; ++a)
+      for (int b = 0; b < nq; ++b) D[a][b] = a == b ? 0 : (A[a][b] ? 1 : 64);
+    for (int c = 0; c < nq; ++c)
+      for (int a = 0; a < nq; ++a)
+        for (int b = 0; b < nq; ++b) D[a][b] = std::min(D[a][b], D[a][c] + D[c][b]);
+    for (int i = 0; i < nq; ++i)
+      for (int j = 0; j < nq; ++j) Q.qd[i][j] = (int8_t)D[order[i]][order[j]];
+  }
+  Q.refine = getenv("NURI_ISO_ROOT_BOUND") ? 0 : 1;
   // histogram resolution: exact bins when every score fits
   int64_t mx = 0;
   for (int i = 0; i < nq; ++i) mx += in.labels[i] < L ? std::max(0, gmax[in.labels[i]]) : 0;
@@ -608,7 +646,7 @@ void topk_iso_batch(nuri_graph* G, int32_t nqueries, const nuri_query* qs, const
   int64_t launches = 0;
   std::vector<Prepared> prep(nqueries);
   for (int i = 0; i < nqueries; ++i)
-    if (!prepare_query(qs[i], ks[i], gmax, g.L, &prep[i]))
+    if (!prepare_query(qs[i], ks[i], gmax, g.L, (flags & NURI_ISO_INDUCED) != 0, &prep[i]))
       NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_iso: query %d is not a connected simple graph", i);
 
   DBuf<IsoQuery> dq;

@@ -40,6 +40,11 @@ struct Err {
 // ------------------------------------------------------------------------------------------
 // stream-ordered device buffers
 // ------------------------------------------------------------------------------------------
+// The library's memory pool on the current device (capi.cu): freed blocks stay cached in it,
+// up to a bound, so that the buffers of one query are reused by the next without going back
+// to the driver.
+cudaMemPool_t device_pool();
+
 template <class T>
 struct DBuf {
   T* p = nullptr;
@@ -64,7 +69,7 @@ struct DBuf {
     reset();
     s = st;
     n = count;
-    if (count) NURI_CUDA(cudaMallocAsync((void**)&p, sizeof(T) * count, st));
+    if (count) NURI_CUDA(cudaMallocFromPoolAsync((void**)&p, sizeof(T) * count, device_pool(), st));
   }
   void reset() {
     if (p) cudaFreeAsync(p, s);
@@ -98,6 +103,10 @@ struct DevGraph {
   const int32_t* oout = nullptr;
   const int32_t* vert_of = nullptr;
   const int32_t* rank_of = nullptr;
+  // core bitmap: adjacency of the last core_n ranks (the densest core of the degeneracy
+  // order), row r - core_base = core_n/64 words; bit (a, b) set iff ranks a, b are adjacent
+  int32_t core_base = 0, core_n = 0;
+  const unsigned long long* core_bits = nullptr;
   const uint8_t* labels = nullptr;
   const int32_t* weights = nullptr;
   const int64_t* lsoff = nullptr;   // [n*L + 1]
@@ -123,6 +132,7 @@ struct nuri_graph {
   cudaStream_t stream = nullptr;
   nuri::DBuf<int64_t> off, ooff, lsoff, lab_off;
   nuri::DBuf<int32_t> adj, deg, oout, vert_of, rank_of, weights, idx_w, idx_d, gmax_w, gmax_d;
+  nuri::DBuf<unsigned long long> core_bits;
   nuri::DBuf<uint8_t> labels;
   nuri::DBuf<int32_t> lab_vert;
   std::vector<int32_t> h_gmax_w, h_gmax_d;  // host copies of the per-label maxima
@@ -132,7 +142,7 @@ struct nuri_graph {
     return off.bytes() + ooff.bytes() + lsoff.bytes() + adj.bytes() + deg.bytes() +
            oout.bytes() + vert_of.bytes() + rank_of.bytes() + weights.bytes() + idx_w.bytes() +
            idx_d.bytes() + gmax_w.bytes() + gmax_d.bytes() + labels.bytes() + lseg_w.bytes() +
-           lseg_d.bytes() + lab_off.bytes() + lab_vert.bytes();
+           lseg_d.bytes() + lab_off.bytes() + lab_vert.bytes() + core_bits.bytes();
   }
 };
 

@@ -191,3 +191,42 @@ def test_rmat_seven_and_eight_vertex_queries_k1000(scale):
         want = orows(g, q, 1000)
         assert grows(b) == want, q
         assert grows(nuri.topk_iso(G, q, 1000)) == want, q
+
+
+def test_induced_matches_vs_oracle_and_brute():
+    """NURI_ISO_INDUCED: only matches whose images of non-adjacent query vertices are
+    non-adjacent; compared with the oracle's induced mode (pinned by brute force) on tiny
+    graphs and on R-MAT 10 / 12 with k up to 1000."""
+    rng = np.random.default_rng(5)
+    for i in range(20):
+        g = _labelled(int(rng.integers(3, 12)), [0.4, 0.7][i % 2], 1700 + i, nlab=2)
+        G = load(g)
+        for q in _shapes(rng, 2, sizes=(2, 3, 4, 5)):
+            for k in (1, 100):
+                want = [(r[0], tuple(r[1]), tuple(r[2])) for r in oracle.topk_iso(g, q, k, induced=True)]
+                assert grows(nuri.topk_iso(G, q, k, induced=True)) == want, (i, q, k)
+                if i % 5 == 0:
+                    assert want == [tuple(r) for r in brute.topk_iso(g, q, k, induced=True)]
+    for scale in (10, 12):
+        g = _rmat_labelled(scale, 16, seed=60 + scale, nlab=4)
+        G = load(g)
+        qs = synth.query_batch(12, seed=scale + 3, size_lo=3, size_hi=7, num_labels=4)
+        got = nuri.topk_iso_batch(G, qs, [1000] * len(qs), induced=True)
+        for q, r in zip(qs, got):
+            want = [(x[0], tuple(x[1]), tuple(x[2])) for x in oracle.topk_iso(g, q, 1000, induced=True)]
+            assert grows(r) == want, q
+
+
+def test_matched_vertex_bound_same_rows_fewer_candidates(monkeypatch):
+    """The bound of an unmatched query vertex taken from the nearest matched image (not only
+    the root's) prunes more and changes no row: equal to the root-only bound and the oracle."""
+    g = _rmat_labelled(12, 16, seed=71)
+    G = load(g)
+    qs = synth.query_batch(16, seed=72, size_lo=5, size_hi=8, num_labels=8)
+    tight = nuri.topk_iso_batch(G, qs, [100] * len(qs))
+    monkeypatch.setenv("NURI_ISO_ROOT_BOUND", "1")
+    loose = nuri.topk_iso_batch(G, qs, [100] * len(qs))
+    monkeypatch.delenv("NURI_ISO_ROOT_BOUND")
+    for q, a, b in zip(qs, tight, loose):
+        assert grows(a) == grows(b) == orows(g, q, 100), q
+    assert tight[0].stats["expansions"] <= loose[0].stats["expansions"]
