@@ -95,6 +95,8 @@ typedef struct nuri_stats {
                               combined into candidate masks (colouring, branching) */
   int64_t dense_records[3];/* cliques: records searched on 2-, 4- and 8-word bitmap rows
                               (65..128, 129..256 and 257..512 candidates)           */
+  int64_t lex_pruned;      /* cliques: search nodes pruned by the tie bound (their cliques
+                              all rank after k known results of the k-th size)      */
 } nuri_stats;
 
 /* A result set.  Row i has score[i]; its vertices are verts[vert_off[i] .. vert_off[i+1])

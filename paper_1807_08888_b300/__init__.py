@@ -65,6 +65,7 @@ class _Stats(ctypes.Structure):
         ("expand_launches", ctypes.c_int64), ("expand_ms", ctypes.c_double),
         ("tail_launches", ctypes.c_int64), ("tail_ms", ctypes.c_double),
         ("tail_words", ctypes.c_int64), ("dense_records", ctypes.c_int64 * 3),
+        ("lex_pruned", ctypes.c_int64),
     ]
 
 

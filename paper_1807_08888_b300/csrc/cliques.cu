@@ -76,6 +76,7 @@ struct QState {
   int64_t work_next;     // dynamic work counter
   unsigned long long expansions, pruned, dequeued, adj_bytes;
   unsigned long long tail_words;  // adjacency-row words combined by the task kernel
+  unsigned long long lex_pruned;  // nodes pruned by the lexicographic tie bound
   int32_t hmax;          // largest clique size recorded so far
   int32_t hist[MAXD + 2];
 };
@@ -423,7 +424,70 @@ struct WideStore {
   const int32_t* reclow;
   int32_t lex_tau;
   int32_t lex_first;
+  // full lexicographic bound: per slot the original id of every candidate (cid), the
+  // candidates in ascending id order (byid) and the record's ids ascending (rid); lexL: the
+  // sorted id list of the (k - c_hi)-th smallest stored result of size lex_tau (null: off)
+  int32_t* cid;
+  uint16_t* byid;
+  int32_t* rid;
+  const int32_t* lexL;
 };
+
+// Does every clique of size tau below the node rank after the list lexL?  The node's
+// smallest possible sorted id list merges the record's ids (rid), the picked candidates and
+// the m smallest candidates of Pn (walking the candidates in id order); it is compared with
+// lexL element by element.  True only when it is larger (equal or smaller: keep the node).
+template <int W>
+__device__ bool lex_list_after(const WideStore& ws, int slot, int nv, const uint16_t* pick,
+                               int depth, const unsigned long long* Pn, int m, int tau) {
+  constexpr int BMW = 64 * W;
+  const int32_t* rid = ws.rid + (int64_t)slot * MAXD;
+  const int32_t* cid = ws.cid + (int64_t)slot * BMW;
+  const uint16_t* byid = ws.byid + (int64_t)slot * BMW;
+  const int p = ws.recP[slot];
+  unsigned long long picked[W];
+#pragma unroll
+  for (int q = 0; q < W; ++q) picked[q] = 0ull;
+  for (int q = 0; q <= depth; ++q) set_bit<W>(picked, pick[q]);
+  int ir = 0, ic = 0, taken = 0;
+  int32_t cand = INT32_MAX;  // id of the next candidate stream element
+  auto next_cand = [&]() {
+    cand = INT32_MAX;
+    while (ic < p) {
+      const int a = byid[ic++];
+      const int qa = a >> 6;
+      unsigned long long pw = 0, pp = 0;
+#pragma unroll
+      for (int q = 0; q < W; ++q)
+        if (q == qa) {
+          pw = picked[q];
+          pp = Pn[q];
+        }
+      const unsigned long long bit = 1ull << (a & 63);
+      if (pw & bit) {
+        cand = cid[a];
+        return;
+      }
+      if ((pp & bit) && taken < m) {
+        ++taken;
+        cand = cid[a];
+        return;
+      }
+    }
+  };
+  next_cand();
+  for (int t = 0; t < tau; ++t) {
+    int32_t x;
+    if (ir < nv && rid[ir] < cand) x = rid[ir++];
+    else {
+      x = cand;
+      next_cand();
+    }
+    const int32_t y = ws.lexL[t];
+    if (x != y) return x > y;
+  }
+  return false;
+}
 
 // Visit the node (record + picks[0..depth], candidates Pn, explored Xn) of a dense record and
 // finish its subtree with colour-ordered branching; if `split` is set and the node has more
@@ -435,7 +499,7 @@ __device__ void dense_node(const Ctx& cx, const WideStore& ws, int slot, int dep
                            uint16_t* pick, unsigned long long* Pn, unsigned long long* Xn,
                            bool split, bool cont, int32_t& t_cache, unsigned long long& my_exp,
                            unsigned long long& my_pruned, unsigned long long& my_words,
-                           bool& limit_hit, bool& out_of_time) {
+                           unsigned long long& my_lex, bool& limit_hit, bool& out_of_time) {
   constexpr int BMW = 64 * W;
   const unsigned long long* rows = ws.rows + (int64_t)slot * BMW * W;
   const int32_t* vmap = ws.vmap + (int64_t)slot * BMW;
@@ -629,16 +693,19 @@ __device__ void dense_node(const Ctx& cx, const WideStore& ws, int slot, int dep
           level_ok = false;
         }
       }
-      // tie-aware pruning: no clique below this node can exceed tau (one more colour class
-      // empties R) and every clique below it would have its smallest id above lex_first
-      // (neither the clique nor any candidate holds a smaller one): at least k known results
-      // rank before each of them
-      if (level_ok && lex && ws.lex_tau == t_cache && size < t_cache && !lowc[depth]) {
+      // tie-aware pruning: when no clique below this node can exceed tau (one more colour
+      // class empties R), every clique below it has size at most tau, and its sorted id list
+      // is at least the node's smallest possible one: the clique's ids with the tau - |node|
+      // smallest ids among the candidates.  If that list ranks after the (k - c_hi)-th stored
+      // result of size tau, at least k known results rank before each of them.  The cheap
+      // first test: neither the clique nor a candidate holds an id up to that result's first.
+      if (level_ok && lex && ws.lex_tau == t_cache && size < t_cache) {
         unsigned long long hit = 0;
 #pragma unroll
         for (int q = 0; q < W; ++q)
           if (q < wa) hit |= Pn[q] & lowm[q];
-        if (!hit) {
+        const bool first_after = !hit && !lowc[depth];
+        if (first_after || ws.lexL) {
           unsigned long long cls[W], R2[W];
 #pragma unroll
           for (int q = 0; q < W; ++q) {
@@ -646,8 +713,11 @@ __device__ void dense_node(const Ctx& cx, const WideStore& ws, int slot, int dep
             R2[q] = R[q];
           }
           colour_class<W>(cls, R2, rows, wa, my_words);
-          if (!any<W>(R2, wa)) {
+          if (!any<W>(R2, wa) &&
+              (first_after ||
+               lex_list_after<W>(ws, slot, nv, pick, depth, Pn, t_cache - size, t_cache))) {
             ++my_pruned;
+            ++my_lex;
             level_ok = false;
           }
         }
@@ -706,7 +776,7 @@ template <int W>
 __global__ void __launch_bounds__(128, 6) k_clique_tasks(Ctx cx, WideStore ws,
                                                       const WTask* __restrict__ in, int64_t nin,
                                                       unsigned long long* next) {
-  unsigned long long my_exp = 0, my_pruned = 0, my_words = 0;
+  unsigned long long my_exp = 0, my_pruned = 0, my_words = 0, my_lex = 0;
   bool limit_hit = false, out_of_time = false;
   int32_t t_cache = ld_volatile(&cx.st->tau);
   while (!out_of_time) {
@@ -728,18 +798,20 @@ __global__ void __launch_bounds__(128, 6) k_clique_tasks(Ctx cx, WideStore ws,
     }
     t_cache = ld_volatile(&cx.st->tau);
     dense_node<W>(cx, ws, T.slot, T.depth, pick, Pn, Xn, true, T.cont != 0, t_cache, my_exp,
-                  my_pruned, my_words, limit_hit, out_of_time);
+                  my_pruned, my_words, my_lex, limit_hit, out_of_time);
   }
   if (limit_hit) atomicOr(&cx.st->err, 1);
   for (int o = 16; o; o >>= 1) {
     my_exp += __shfl_xor_sync(0xffffffffu, my_exp, o);
     my_pruned += __shfl_xor_sync(0xffffffffu, my_pruned, o);
     my_words += __shfl_xor_sync(0xffffffffu, my_words, o);
+    my_lex += __shfl_xor_sync(0xffffffffu, my_lex, o);
   }
   if ((threadIdx.x & 31) == 0) {
     atomicAdd(&cx.st->expansions, my_exp);
     atomicAdd(&cx.st->pruned, my_pruned);
     atomicAdd(&cx.st->tail_words, my_words);
+    atomicAdd(&cx.st->lex_pruned, my_lex);
   }
 }
 
@@ -1123,6 +1195,25 @@ __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
           ws.recN[slot] = nv;
           ws.recP[slot] = p;
         }
+        if (ws.cid) {
+          // ids of the candidates, their order by id (rank by counting), the record's ids
+          int32_t* cid = ws.cid + (int64_t)slot * BMW;
+          for (int a = lane; a < p; a += 32) cid[a] = __ldg(g.vert_of + sp[perm[a]]);
+          __syncwarp();
+          for (int a = lane; a < p; a += 32) {
+            const int32_t x = cid[a];
+            int r = 0;
+            for (int b2 = 0; b2 < p; ++b2) r += cid[b2] < x ? 1 : 0;
+            ws.byid[(int64_t)slot * BMW + r] = (uint16_t)a;
+          }
+          int32_t* rid = ws.rid + (int64_t)slot * MAXD;
+          for (int a = lane; a < nv; a += 32) {
+            const int32_t x = __ldg(g.vert_of + sV[w][a]);
+            int r = 0;
+            for (int b2 = 0; b2 < nv; ++b2) r += __ldg(g.vert_of + sV[w][b2]) < x ? 1 : 0;
+            rid[r] = x;
+          }
+        }
         __threadfence_block();
         __syncwarp();
         for (int i = p - 1 - lane; i >= 0 && !out_of_time; i -= 32) {
@@ -1157,9 +1248,9 @@ __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
           } else {
             uint16_t pk[MAXD + 1];
             pk[0] = (uint16_t)v0;
-            unsigned long long words_here = 0;  // counted for the task kernel only
+            unsigned long long words_here = 0, lex_here = 0;  // counted for the task kernel
             dense_node<W>(cx, ws, slot, 0, pk, Pi, Xi, false, false, t_cache, my_exp,
-                          my_pruned, words_here, limit_hit, out_of_time);
+                          my_pruned, words_here, lex_here, limit_hit, out_of_time);
           }
         }
       } else {
@@ -1646,6 +1737,99 @@ __global__ void k_greedy_tau(DevGraph g, const int32_t* __restrict__ seeds, int6
   }
 }
 
+// Warm start for seeds whose candidates all lie in the core bitmap (the dense core of the
+// order, where near-cliques live): one warp per seed orders the candidates by their number of
+// neighbours among the candidates (bitmap popcounts), then adds them greedily in that order
+// when adjacent to every one added before, and publishes subset_tau of the clique's size.
+// Like k_greedy_tau it records nothing (the answer is unchanged).  Seeds with more than
+// kGreedyCoreMax candidates or outside the core are skipped.
+constexpr int kGreedyCoreMax = 1024;
+constexpr int kGreedyCoreWarps = 4;
+__global__ void __launch_bounds__(kGreedyCoreWarps * 32)
+    k_greedy_core_tau(DevGraph g, const int32_t* __restrict__ seeds, int64_t nseeds, int32_t k,
+                      int32_t* __restrict__ tau) {
+  __shared__ unsigned long long sP[kGreedyCoreWarps][64], sC[kGreedyCoreWarps][64];
+  __shared__ unsigned long long sKey[kGreedyCoreWarps][kGreedyCoreMax];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned FULL = 0xffffffffu;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int cw = g.core_n >> 6;  // <= 64 words
+  unsigned long long* P = sP[w];
+  unsigned long long* C = sC[w];
+  unsigned long long* key = sKey[w];
+  for (int64_t it = warp; it < nseeds; it += nwarps) {
+    const int32_t v = seeds[it];
+    const int64_t b = g.ooff[v];
+    const int p = (int)(g.ooff[v + 1] - b);
+    if (p == 0 || p > kGreedyCoreMax || g.oout[b] < g.core_base) continue;
+    for (int q = lane; q < 64; q += 32) {
+      P[q] = 0ull;
+      C[q] = 0ull;
+    }
+    __syncwarp();
+    for (int t = lane; t < p; t += 32) {
+      const int x = g.oout[b + t] - g.core_base;
+      atomicOr(&P[x >> 6], 1ull << (x & 63));
+    }
+    __syncwarp();
+    // key = (neighbours among the candidates) << 32 | (inverted core index: lower first)
+    int n2 = 1;
+    while (n2 < p) n2 <<= 1;
+    for (int t = lane; t < n2; t += 32) {
+      unsigned long long kk = 0ull;
+      if (t < p) {
+        const int x = g.oout[b + t] - g.core_base;
+        const unsigned long long* row = g.core_bits + (int64_t)x * cw;
+        int d = 0;
+        for (int q = 0; q < cw; ++q) d += __popcll(__ldg(row + q) & P[q]);
+        kk = ((unsigned long long)(d + 1) << 32) | (0xFFFFFFFFull - (unsigned)x);
+      }
+      key[t] = kk;
+    }
+    __syncwarp();
+    // bitonic sort, descending
+    for (int kk = 2; kk <= n2; kk <<= 1)
+      for (int j = kk >> 1; j > 0; j >>= 1) {
+        for (int i = lane; i < n2; i += 32) {
+          const int l = i ^ j;
+          if (l > i) {
+            const unsigned long long a = key[i], c = key[l];
+            const bool desc = (i & kk) == 0;
+            if (desc ? (a < c) : (a > c)) {
+              key[i] = c;
+              key[l] = a;
+            }
+          }
+        }
+        __syncwarp();
+      }
+    // greedy: add each candidate, in that order, that is adjacent to every one added before
+    int size = 1;
+    for (int t = 0; t < p; ++t) {
+      if ((t & 31) == 0) {  // cannot beat the current bound: stop (decided by lane 0)
+        int stop = 0;
+        if (lane == 0) stop = size + (p - t) <= ld_volatile(tau);
+        if (__shfl_sync(FULL, stop, 0)) break;
+      }
+      const int x = (int)(0xFFFFFFFFull - (key[t] & 0xFFFFFFFFull));
+      const unsigned long long* row = g.core_bits + (int64_t)x * cw;
+      bool ok = true;
+      for (int q = lane; q < cw; q += 32) ok &= (__ldg(row + q) & C[q]) == C[q];
+      if (__all_sync(FULL, ok)) {
+        if (lane == 0) C[x >> 6] |= 1ull << (x & 63);
+        ++size;
+      }
+      __syncwarp();
+    }
+    if (lane == 0) {
+      const int st = subset_tau(size, k);
+      if (st > 0) atomicMax(tau, st);
+    }
+    __syncwarp();
+  }
+}
+
 struct BucketPtrs {
   Rec* base[NB];
   int64_t fill[NB];  // current counts before the scatter
@@ -1740,6 +1924,10 @@ struct DenseBufs {
   DBuf<int32_t> reclow2, reclow4, reclow8;
   DBuf<int32_t> lexbuf;                      // smallest id of each size-tau result
   DBuf<unsigned long long> lexcnt;
+  DBuf<int32_t> cid2, cid4, cid8, rid2, rid4, rid8;  // full lexicographic bound, per slot
+  DBuf<uint16_t> byid2, byid4, byid8;
+  DBuf<int32_t> lexrows;                     // sorted id lists of the size-tau results
+  DBuf<int32_t> lexL;                        // the list the bound compares with
   bool lex_allowed = false;  // all-cliques ranking, pruning on, ties not kept
   int64_t qcap = 0;          // current entries of each queue
   int64_t qmax = 0;          // entries a queue may grow to (NURI_TASK_QUEUE, default 16M)
@@ -1756,7 +1944,7 @@ int64_t task_queue_max() {
 // Device bytes of one store slot of the W-word tier (rows, vertex map, record, masks).
 int64_t slot_bytes(int W) {
   const int64_t bmw = 64 * W;
-  return bmw * W * 8 + bmw * 4 + MAXD * 4 + 8 + W * 8 + 4;
+  return bmw * W * 8 + bmw * 4 + MAXD * 4 + 8 + W * 8 + 4 + bmw * 6 + MAXD * 4;
 }
 
 // Store slots one dense pass uses at most: the records of a tier are searched in chunks of
@@ -1774,6 +1962,9 @@ WideStore make_store(DenseBufs& B, int W, int64_t nrec, cudaStream_t s) {
   DBuf<int32_t>& recP = W == 2 ? B.recP2 : (W == 4 ? B.recP4 : B.recP8);
   DBuf<unsigned long long>& low = W == 2 ? B.low2 : (W == 4 ? B.low4 : B.low8);
   DBuf<int32_t>& reclow = W == 2 ? B.reclow2 : (W == 4 ? B.reclow4 : B.reclow8);
+  DBuf<int32_t>& cid = W == 2 ? B.cid2 : (W == 4 ? B.cid4 : B.cid8);
+  DBuf<int32_t>& rid = W == 2 ? B.rid2 : (W == 4 ? B.rid4 : B.rid8);
+  DBuf<uint16_t>& byid = W == 2 ? B.byid2 : (W == 4 ? B.byid4 : B.byid8);
   if ((int64_t)recN.n < nrec) {
     int64_t cap = std::max<int64_t>(nrec, 256);
     rows.alloc(cap * bmw * W, s);
@@ -1784,6 +1975,9 @@ WideStore make_store(DenseBufs& B, int W, int64_t nrec, cudaStream_t s) {
     if (B.lex_allowed) {
       low.alloc(cap * W, s);
       reclow.alloc(cap, s);
+      cid.alloc(cap * bmw, s);
+      byid.alloc(cap * bmw, s);
+      rid.alloc(cap * MAXD, s);
     }
   }
   if (!B.counters.p) B.counters.alloc(3, s);
@@ -1815,6 +2009,10 @@ WideStore make_store(DenseBufs& B, int W, int64_t nrec, cudaStream_t s) {
   ws.reclow = reclow.p;
   ws.lex_tau = INT32_MIN;
   ws.lex_first = 0;
+  ws.cid = B.lex_allowed ? cid.p : nullptr;
+  ws.byid = B.lex_allowed ? byid.p : nullptr;
+  ws.rid = B.lex_allowed ? rid.p : nullptr;
+  ws.lexL = nullptr;
   return ws;
 }
 
@@ -1907,6 +2105,30 @@ __global__ void k_row_minid(const Rec* __restrict__ res, int64_t n, int32_t tau,
   }
 }
 
+// The sorted original-id list of every stored result of size tau (tau ids each, rank by
+// counting inside the row; one warp per row).
+__global__ void k_rows_sorted(const Rec* __restrict__ res, int64_t n, int32_t tau,
+                              const int32_t* __restrict__ vert_of, int32_t* __restrict__ out,
+                              unsigned long long* __restrict__ cnt, int64_t cap) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < n; i += nwarps) {
+    if (res[i].nv != tau) continue;
+    unsigned long long slot = 0;
+    if (lane == 0) slot = atomicAdd(cnt, 1ull);
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    if ((int64_t)slot >= cap) continue;  // room for cap rows
+    int32_t* o = out + (int64_t)slot * tau;
+    for (int a = lane; a < tau; a += 32) {
+      const int32_t x = __ldg(vert_of + res[i].V[a]);
+      int r = 0;
+      for (int b = 0; b < tau; ++b) r += __ldg(vert_of + res[i].V[b]) < x ? 1 : 0;
+      o[r] = x;
+    }
+  }
+}
+
 // Per store slot: the candidates with vertex id <= first (mask of W words) and whether the
 // record itself holds such a vertex.  One warp per slot.
 template <int W>
@@ -1967,6 +2189,7 @@ void update_lex(const Ctx& cx, WideStore& ws, ResultStore& rs, DenseBufs& B, cud
   const int64_t need = (int64_t)cx.k - c_hi;
   if (tau < 1 || tau > MAXD || need <= 0 || rc > rs.cap || rc <= 0) {
     ws.lex_tau = INT32_MIN;
+    ws.lexL = nullptr;
     return;
   }
   if ((int64_t)B.lexbuf.n < rc) B.lexbuf.alloc(std::max<int64_t>(rc, 4096), s);
@@ -1980,6 +2203,7 @@ void update_lex(const Ctx& cx, WideStore& ws, ResultStore& rs, DenseBufs& B, cud
   NURI_CUDA(cudaStreamSynchronize(s));
   if ((int64_t)m < need) {
     ws.lex_tau = INT32_MIN;
+    ws.lexL = nullptr;
     return;
   }
   std::vector<int32_t> ids(m);
@@ -1987,6 +2211,31 @@ void update_lex(const Ctx& cx, WideStore& ws, ResultStore& rs, DenseBufs& B, cud
   NURI_CUDA(cudaStreamSynchronize(s));
   std::nth_element(ids.begin(), ids.begin() + (need - 1), ids.end());
   const int32_t first = ids[need - 1];
+  // the full list: the need-th smallest sorted id list among the size-tau results
+  if (ws.cid) {
+    if ((int64_t)B.lexrows.n < (int64_t)m * tau) B.lexrows.alloc((int64_t)m * tau, s);
+    NURI_CUDA(cudaMemsetAsync(B.lexcnt.p, 0, 8, s));
+    k_rows_sorted<<<std::max(1, std::min<int>((int)((rc + 7) / 8), sm_count() * 16)), 256, 0, s>>>(
+        rs.buf.p, rc, tau, cx.g.vert_of, B.lexrows.p, B.lexcnt.p, (int64_t)m);
+    NURI_CUDA(cudaGetLastError());
+    std::vector<int32_t> rows((size_t)m * tau);
+    NURI_CUDA(cudaMemcpyAsync(rows.data(), B.lexrows.p, sizeof(int32_t) * m * tau,
+                              cudaMemcpyDeviceToHost, s));
+    NURI_CUDA(cudaStreamSynchronize(s));
+    std::vector<int64_t> order(m);
+    for (int64_t i = 0; i < (int64_t)m; ++i) order[i] = i;
+    std::nth_element(order.begin(), order.begin() + (need - 1), order.end(),
+                     [&](int64_t a, int64_t b) {
+                       return std::lexicographical_compare(
+                           rows.begin() + a * tau, rows.begin() + a * tau + tau,
+                           rows.begin() + b * tau, rows.begin() + b * tau + tau);
+                     });
+    if ((int64_t)B.lexL.n < tau) B.lexL.alloc(MAXD, s);
+    NURI_CUDA(cudaMemcpyAsync(B.lexL.p, rows.data() + order[need - 1] * tau,
+                              sizeof(int32_t) * tau, cudaMemcpyHostToDevice, s));
+    NURI_CUDA(cudaStreamSynchronize(s));
+    ws.lexL = B.lexL.p;
+  }
   if (ws.lex_tau == tau && ws.lex_first == first) return;  // masks still valid
   unsigned long long nslots = 0;
   NURI_CUDA(cudaMemcpyAsync(&nslots, B.counters.p, 8, cudaMemcpyDeviceToHost, s));
@@ -2305,6 +2554,13 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
       ++launches;
       k_greedy_tau<<<gblocks, 256, 0, s>>>(g, svals2.p, take1, k, gbuf.p, gtau.p);
     }
+    if (take0 > 0 && g.core_bits) {
+      ++launches;
+      k_greedy_core_tau<<<std::max<int64_t>(1, std::min<int64_t>((take0 + kGreedyCoreWarps - 1) /
+                                                                      kGreedyCoreWarps,
+                                                                  sm_count() * 8)),
+                          kGreedyCoreWarps * 32, 0, s>>>(g, svals2.p + c0, take0, k, gtau.p);
+    }
     NURI_CUDA(cudaGetLastError());
     int32_t gt = INT32_MIN;
     NURI_CUDA(cudaMemcpyAsync(&gt, gtau.p, 4, cudaMemcpyDeviceToHost, s));
@@ -2381,7 +2637,8 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
     };
     // the first chunk is small: with tau still unset every node is a result, so a wide first
     // launch would fill the result set with small cliques; the chunk doubles every seed round
-    int64_t seed_chunk = 512;
+    // (once the warm start has set tau, results below it are not stored: start wide)
+    int64_t seed_chunk = tau_init > 1 ? (1 << 16) : 512;
 
     while (true) {
       NURI_CUDA(cudaMemcpyAsync(&hs, st.p, sizeof(hs), cudaMemcpyDeviceToHost, s));
@@ -2692,6 +2949,7 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
   stats.dequeued += (int64_t)hs.dequeued;
   stats.adj_bytes += (int64_t)hs.adj_bytes;
   stats.tail_words = (int64_t)hs.tail_words;
+  stats.lex_pruned = (int64_t)hs.lex_pruned;
   stats.tail_ms = tail.ms;
   stats.tail_launches = tail.launches;
   stats.results_stored = hs.res_count;

@@ -153,11 +153,14 @@ __global__ void k_peel_list(const int32_t* __restrict__ batch, int32_t n,
 // front/nfront: the current front (batch b), k, b: the current level and batch.
 // out[0] = the largest k reached, out[1] = 0 on success, 1 if a front came out empty while
 // vertices remained (cannot happen; reported instead of looping).
+constexpr int64_t kHeavyRow = 512;  // rows longer than this are walked by the whole CTA
+constexpr int kHeavyList = 256;     // heavy rows per batch handled that way (the rest by warps)
 __global__ void __launch_bounds__(1024) k_peel_tail(
     const int64_t* __restrict__ off, const int32_t* __restrict__ adj, int32_t* __restrict__ rem,
     int32_t* __restrict__ batch, int32_t* la, int32_t* lb, int32_t nlist, int32_t* fa,
     int32_t* fb, int32_t nfront0, int32_t k0, int32_t b0, int32_t* out) {
-  __shared__ int32_t s_nlist, s_nfront, s_nnext, s_k, s_min, s_cnt;
+  __shared__ int32_t s_nlist, s_nfront, s_nnext, s_k, s_min, s_cnt, s_nheavy;
+  __shared__ int32_t s_heavy[kHeavyList];
   __shared__ int64_t s_remaining;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
@@ -167,6 +170,7 @@ __global__ void __launch_bounds__(1024) k_peel_tail(
   int32_t* next = fb;
   int32_t b = b0;
   if (tid == 0) {
+    s_nheavy = 0;
     s_nlist = nlist;
     s_nfront = nfront0;
     s_nnext = 0;
@@ -225,16 +229,34 @@ __global__ void __launch_bounds__(1024) k_peel_tail(
       }
     }
     const int32_t k = s_k, nf = s_nfront;
+    // light front vertices: one warp each; heavy ones (long rows): the whole CTA, one at a
+    // time, so that a hub's row is not walked by one warp's chain of atomics
+    auto drop = [&](int32_t u) {
+      if (*(volatile int32_t*)(batch + u) >= 0) return;
+      const int32_t old = atomicSub(rem + u, 1);
+      if (old - 1 <= k && atomicCAS(batch + u, -1, b + 1) == -1) next[atomicAdd(&s_nnext, 1)] = u;
+    };
     for (int w = warp; w < nf; w += nwarps) {
       const int32_t v = front[w];
-      for (int64_t t = off[v] + lane; t < off[v + 1]; t += 32) {
-        const int32_t u = adj[t];
-        if (*(volatile int32_t*)(batch + u) >= 0) continue;
-        const int32_t old = atomicSub(rem + u, 1);
-        if (old - 1 <= k && atomicCAS(batch + u, -1, b + 1) == -1) next[atomicAdd(&s_nnext, 1)] = u;
+      if (off[v + 1] - off[v] > kHeavyRow) {
+        int slot = -1;
+        if (lane == 0) slot = atomicAdd(&s_nheavy, 1);
+        slot = __shfl_sync(0xffffffffu, slot, 0);
+        if (slot < kHeavyList) {
+          if (lane == 0) s_heavy[slot] = v;
+          continue;
+        }
       }
+      for (int64_t t = off[v] + lane; t < off[v + 1]; t += 32) drop(adj[t]);
     }
     __syncthreads();
+    const int nh = min(s_nheavy, kHeavyList);
+    for (int h = 0; h < nh; ++h) {
+      const int32_t v = s_heavy[h];
+      for (int64_t t = off[v] + tid; t < off[v + 1]; t += nthr) drop(adj[t]);
+    }
+    __syncthreads();
+    if (tid == 0) s_nheavy = 0;
     {
       int32_t* t = front;
       front = next;

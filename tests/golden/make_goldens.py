@@ -45,6 +45,33 @@ CLIQUE_CASES = {
     "er1000_p033_s5": ("er_small", (1000, 0.33, 5)),
 }
 
+# the headline recipe (Chung-Lu, mean degree 20, exponent 2.1, 50 planted cliques of 15..30)
+# at sizes the Bron-Kerbosch oracle finishes (n = 1M does not: Algorithm 1 stops incomplete
+# after 10^9 expansions, Bron-Kerbosch runs past half an hour on the hub block)
+CHUNGLU_CASES = {
+    "chunglu100k": (100_000, 20.0, 2.1, 50, 15, 30, 0),
+}
+
+
+def chunglu_graph(name):
+    import synth
+    return synth.chung_lu_planted(*CHUNGLU_CASES[name])
+
+
+def make_chunglu(name, k=100):
+    import oracle
+    g = chunglu_graph(name)
+    t = time.time()
+    allr = oracle.bk_cliques(g, k, False)
+    out = {"case": name, "recipe": list(CHUNGLU_CASES[name]), "sha256_graph": g.sha256(),
+           "source": "oracle.bk_cliques (Bron-Kerbosch, pivoting, degeneracy order), "
+                     "all-cliques ranking",
+           "oracle_seconds": time.time() - t,
+           "all": [[r[0], list(r[1])] for r in allr]}
+    with open(os.path.join(HERE, f"cliques_{name}.json"), "w") as f:
+        json.dump(out, f, separators=(",", ":"))
+    print(name, out["oracle_seconds"], flush=True)
+
 
 def clique_graph(name):
     import synth
@@ -139,6 +166,7 @@ def make_patterns_rmat18z(Ms=(1, 2, 3, 4, 5)):
 CASES = {
     "cliques_er1200": lambda: make_cliques("er1200_p025_s91"),
     "cliques_er1000": lambda: make_cliques("er1000_p033_s5", k_all=300, k_max=100),
+    "cliques_chunglu100k": lambda: make_chunglu("chunglu100k"),
     "iso_rmat20": make_iso_rmat20,
     "patterns_rmat18z": make_patterns_rmat18z,
 }

@@ -310,3 +310,41 @@ def test_chung_lu_config_properties(monkeypatch):
     small = nuri.topk_cliques(G, 100)
     monkeypatch.delenv("NURI_RESULT_CAP")
     assert [(r[0], r[1]) for r in small] == got
+
+
+def _near_clique(n, core, missing, p_bg, seed):
+    """A clique on `core` random vertices minus `missing` disjoint pairs (2^missing tied
+    maximum cliques), plus G(n, p_bg) background edges; ids randomly placed."""
+    rng = np.random.default_rng(seed)
+    members = rng.choice(n, core, replace=False)
+    gone = {tuple(sorted(x)) for x in members[:2 * missing].reshape(missing, 2).tolist()}
+    pairs = [(int(a), int(b)) for a, b in itertools.combinations(sorted(members.tolist()), 2)
+             if (a, b) not in gone]
+    bg = synth.er_small(n, p_bg, seed=seed + 1)
+    src = np.concatenate([np.array([a for a, _ in pairs], np.int32), bg.src])
+    dst = np.concatenate([np.array([b for _, b in pairs], np.int32), bg.dst])
+    return synth.Graph(n, src, dst, name=f"nearclique{core}m{missing}s{seed}")
+
+
+@pytest.mark.parametrize("core,missing", [(100, 10), (266, 12)])
+def test_tie_bound_on_tied_maximum_cliques(monkeypatch, core, missing):
+    """Many tied maximum cliques (2^missing of size core - missing): the k rows are the k
+    lexicographically smallest, which strict pruning alone finds only by enumerating every
+    tie.  The tie bound (a node whose smallest possible sorted id list ranks after the k-th
+    known tied result is dropped) must prune and must not change a row: equal to the
+    Bron-Kerbosch oracle and to the search with the bound switched off."""
+    g = _near_clique(core + 60, core, missing, 0.05, seed=core)
+    G = load(g)
+    ref = [(r[0], tuple(r[1])) for r in oracle.bk_cliques(g, 300, False)]
+    assert ref[0][0] == ref[-1][0] >= core - missing  # at least 300 tied maximum cliques
+    pruned = 0
+    for k in (1, 5, 50, 300):
+        got = nuri.topk_cliques(G, k)
+        assert [(r[0], r[1]) for r in got] == ref[:k], k
+        pruned += got.stats["lex_pruned"]
+    assert pruned > 0
+    monkeypatch.setenv("NURI_NO_LEX", "1")
+    off = nuri.topk_cliques(G, 50)
+    monkeypatch.delenv("NURI_NO_LEX")
+    assert [(r[0], r[1]) for r in off] == ref[:50]
+    assert off.stats["lex_pruned"] == 0

@@ -19,7 +19,8 @@ pytestmark = pytest.mark.gpu
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 sys.path.insert(0, GOLD)
-from make_goldens import CLIQUE_CASES, clique_graph, row_digest  # noqa: E402
+from make_goldens import (CHUNGLU_CASES, CLIQUE_CASES, chunglu_graph, clique_graph,  # noqa: E402
+                          row_digest)
 
 
 def _golden(name):
@@ -58,6 +59,24 @@ def test_cliques_eight_word_tier_vs_bron_kerbosch(case):
         del os.environ["NURI_TASK_SPLIT"]
         del os.environ["NURI_NO_LEX"]
     assert [(r[0], r[1]) for r in again] == allr[:100]
+
+
+@pytest.mark.parametrize("case", sorted(CHUNGLU_CASES))
+def test_cliques_headline_recipe_vs_bron_kerbosch(case):
+    """The headline's own recipe (Chung-Lu power law, mean degree 20, exponent 2.1, 50
+    planted cliques of 15..30) at the largest size the oracle finishes: top-100 by size with
+    the lexicographic tie-break, row for row, with the autotuned and the default task
+    granularity."""
+    d = _golden(f"cliques_{case}.json")
+    g = chunglu_graph(case)
+    assert g.sha256() == d["sha256_graph"]
+    G = nuri.load_graph(g.n, g.src, g.dst)
+    want = [(r[0], tuple(r[1])) for r in d["all"]]
+    for k in (1, 10, 100):
+        assert [(r[0], r[1]) for r in nuri.topk_cliques(G, k)] == want[:k], k
+    nuri.tune_cliques(G, 100)
+    assert [(r[0], r[1]) for r in nuri.topk_cliques(G, 100)] == want
+    assert [(r[0], r[1]) for r in nuri.topk_batch(G, [("clique", 100)])[0]] == want
 
 
 def test_iso_rmat20_sixty_four_queries_vs_oracle():
