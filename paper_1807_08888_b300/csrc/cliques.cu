@@ -387,7 +387,7 @@ __device__ __forceinline__ void and_live(unsigned long long* out, const unsigned
 // continuation tasks (nodes already visited, with the candidates not yet branched on), so the
 // next wave spreads that subtree over the GPU instead of leaving it to one lane.
 // ---------------------------------------------------------------------------------------------
-constexpr int TPICKS = 28;  // vertices a task can hold below its record
+constexpr int kSliceNodes = 1 << 14;  // nodes a lane searches before it hands its stack on
 // Device memory bounds of one query's buffers (they make the server's admission estimate an
 // upper bound): records handed to the dense tiers or sent back per round, and the dense store
 constexpr int64_t kRoundRecs = 1 << 16;
@@ -396,11 +396,21 @@ constexpr int64_t kStoreBytes = 256ll << 20;
 
 struct WTask {
   int32_t slot;
-  int16_t depth;  // picks[0..depth] are the vertices added below the record
+  int16_t depth;  // depth + 1 candidates are picked below the record
   int16_t cont;   // 1: the node was visited already; only its branching remains
-  uint16_t picks[TPICKS];
+  unsigned long long C[KWIDE];            // the picked candidates (a set: any depth)
   unsigned long long P[KWIDE], X[KWIDE];  // X only in maximal mode
 };
+
+// The picked candidates pick[0..d] of a node as a task's set.
+__device__ __forceinline__ void write_picks(WTask* t, const uint16_t* pick, int d) {
+  unsigned long long c[KWIDE];
+#pragma unroll
+  for (int q = 0; q < KWIDE; ++q) c[q] = 0ull;
+  for (int q = 0; q <= d; ++q) set_bit<KWIDE>(c, pick[q]);
+#pragma unroll
+  for (int q = 0; q < KWIDE; ++q) t->C[q] = c[q];
+}
 
 struct WideStore {
   unsigned long long* rows;  // per slot: BMW * W words (row i = words i*W .. i*W+W)
@@ -545,7 +555,7 @@ __device__ void dense_node(const Ctx& cx, const WideStore& ws, int slot, int dep
     limit_hit = true;
     return;
   }
-  if (split && depth + 1 < TPICKS && popc<W>(Pn, wa) > ws.split_bits &&
+  if (split && depth + 2 < MAXD && popc<W>(Pn, wa) > ws.split_bits &&
       (int64_t)ld_volatile(ws.q_count) < ws.q_cap / 8) {
     // children as tasks, in colour order: count the viable ones, reserve their queue slots,
     // then emit them
@@ -590,8 +600,8 @@ __device__ void dense_node(const Ctx& cx, const WideStore& ws, int slot, int dep
         my_words += wa;
         t->slot = slot;
         t->depth = (int16_t)(depth + 1);
-        for (int q = 0; q <= depth; ++q) t->picks[q] = pick[q];
-        t->picks[depth + 1] = (uint16_t)v;
+        pick[depth + 1] = (uint16_t)v;
+        write_picks(t, pick, depth + 1);
 #pragma unroll
         for (int q = 0; q < KWIDE; ++q) {
           unsigned long long rq = q < W ? rows[v * W + q] : 0ull;
@@ -636,10 +646,12 @@ __device__ void dense_node(const Ctx& cx, const WideStore& ws, int slot, int dep
     if (fresh) {
       fresh = false;
       const int size = nv + depth + 1;
-      // hand the rest of the stack on once the wave's input is used up (and there is room):
-      // the current node and every level below it that still has vertices to branch on
-      if (split && ++local >= 16 && (local & 15) == 0 && depth < TPICKS &&
-          (int64_t)ld_volatile(ws.in_next) >= ws.in_n &&
+      // hand the rest of the stack on once the wave's input is used up, or once this lane
+      // has searched kSliceNodes nodes (so that no wave runs long between the host's
+      // threshold and tie-bound updates), when there is room: the current node and every
+      // level below it that still has vertices to branch on
+      if (split && ++local >= 16 && (local & 15) == 0 &&
+          ((int64_t)ld_volatile(ws.in_next) >= ws.in_n || local >= kSliceNodes) &&
           (int64_t)ld_volatile(ws.q_count) < ws.q_cap / 2) {
         int r = any<W>(Pn, wa) ? 1 : 0;
         for (int l = base_depth; l < depth; ++l) r += any<W>(stkR[l], wa) ? 1 : 0;
@@ -655,7 +667,7 @@ __device__ void dense_node(const Ctx& cx, const WideStore& ws, int slot, int dep
             t->slot = slot;
             t->depth = (int16_t)l;
             t->cont = 1;
-            for (int q = 0; q <= l; ++q) t->picks[q] = pick[q];
+            write_picks(t, pick, l);
 #pragma unroll
             for (int q = 0; q < KWIDE; ++q) {
               t->P[q] = q < wa ? PL[q] : 0ull;
@@ -789,7 +801,17 @@ __global__ void __launch_bounds__(128, 6) k_clique_tasks(Ctx cx, WideStore ws,
     const WTask& T = in[t];
     if (T.slot < 0) continue;
     uint16_t pick[MAXD + 1];
-    for (int q = 0; q <= T.depth; ++q) pick[q] = T.picks[q];
+    {
+      int d = 0;
+#pragma unroll
+      for (int q = 0; q < KWIDE; ++q) {
+        unsigned long long c = T.C[q];
+        while (c) {
+          pick[d++] = (uint16_t)(q * 64 + __ffsll((long long)c) - 1);
+          c &= c - 1;
+        }
+      }
+    }
     unsigned long long Pn[W], Xn[W];
 #pragma unroll
     for (int q = 0; q < W; ++q) {
@@ -1239,7 +1261,8 @@ __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
             t->slot = slot;
             t->depth = 0;
             t->cont = 0;
-            t->picks[0] = (uint16_t)v0;
+            const uint16_t pk0 = (uint16_t)v0;
+            write_picks(t, &pk0, 0);
 #pragma unroll
             for (int q = 0; q < KWIDE; ++q) {
               t->P[q] = q < W ? Pi[q] : 0ull;
@@ -2018,14 +2041,37 @@ WideStore make_store(DenseBufs& B, int W, int64_t nrec, cudaStream_t s) {
 
 // Candidate results of size >= tau, copied from `in` to `out` (order not kept: the top-k merge
 // sorts).  Rows below tau can never enter the top k, since tau only rises.
+// With a tie list (lexL, for rows of size lex_tau): a row of that size whose sorted ids rank
+// after lexL is dropped too (at least k known rows rank before it).  vert_of maps the row's
+// ranks to ids.
 __global__ void k_compact_results(const Rec* __restrict__ in, int64_t n, int32_t tau,
-                                  Rec* __restrict__ out, unsigned long long* __restrict__ cnt) {
+                                  Rec* __restrict__ out, unsigned long long* __restrict__ cnt,
+                                  const int32_t* __restrict__ lexL, int32_t lex_tau,
+                                  const int32_t* __restrict__ vert_of) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = warp; i < n; i += nwarps) {  // one warp per row
     const int nv = in[i].nv;
     if (nv < tau) continue;
+    if (lexL && nv == lex_tau) {
+      // the first position where the sorted row and lexL differ decides
+      int first = INT32_MAX;
+      bool after = false;
+      for (int a = lane; a < nv; a += 32) {
+        const int32_t x = __ldg(vert_of + in[i].V[a]);
+        int r = 0;
+        for (int b = 0; b < nv; ++b) r += __ldg(vert_of + in[i].V[b]) < x ? 1 : 0;
+        if (x != lexL[r] && r < first) {
+          first = r;
+          after = x > lexL[r];
+        }
+      }
+      int best = first;
+      for (int o = 16; o; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+      const bool drop = __any_sync(0xffffffffu, first == best && best != INT32_MAX && after);
+      if (drop) continue;
+    }
     unsigned long long slot = 0;
     if (lane == 0) slot = atomicAdd(cnt, 1ull);
     slot = __shfl_sync(0xffffffffu, slot, 0);
@@ -2049,7 +2095,8 @@ struct ResultStore {
 // times the rows kept, at least the current capacity), so that a long query does not
 // overflow the set with cliques that tau has since passed.  A set that has already
 // overflowed (rows lost) is left alone: the pass is then re-run with the final tau.
-void compact_results(Ctx& cx, ResultStore& rs, cudaStream_t s) {
+void compact_results(Ctx& cx, ResultStore& rs, cudaStream_t s, const int32_t* lexL = nullptr,
+                     int32_t lex_tau = INT32_MIN) {
   // a caller's copy of the context may predate a compaction made further down: take the
   // current buffer first, whatever happens below
   cx.res = rs.buf.p;
@@ -2065,7 +2112,7 @@ void compact_results(Ctx& cx, ResultStore& rs, cudaStream_t s) {
   DBuf<Rec> nb;
   nb.alloc(rs.cap, s);
   k_compact_results<<<std::max(1, std::min<int>((int)((rc + 7) / 8), sm_count() * 16)), 256, 0, s>>>(
-      rs.buf.p, rc, tau, nb.p, rs.cnt.p);
+      rs.buf.p, rc, tau, nb.p, rs.cnt.p, lexL, lex_tau, cx.g.vert_of);
   NURI_CUDA(cudaGetLastError());
   unsigned long long kept = 0;
   NURI_CUDA(cudaMemcpyAsync(&kept, rs.cnt.p, 8, cudaMemcpyDeviceToHost, s));
@@ -2211,19 +2258,22 @@ void update_lex(const Ctx& cx, WideStore& ws, ResultStore& rs, DenseBufs& B, cud
   NURI_CUDA(cudaStreamSynchronize(s));
   std::nth_element(ids.begin(), ids.begin() + (need - 1), ids.end());
   const int32_t first = ids[need - 1];
-  // the full list: the need-th smallest sorted id list among the size-tau results
+  // the full list: the need-th smallest sorted id list among (at most mcap of) the size-tau
+  // results.  Taken over a subset it is no smaller than over all of them, and at least need
+  // stored results are at or below it, so the bound stays valid (only weaker)
   if (ws.cid) {
-    if ((int64_t)B.lexrows.n < (int64_t)m * tau) B.lexrows.alloc((int64_t)m * tau, s);
+    const int64_t mcap = std::min<int64_t>((int64_t)m, std::max<int64_t>(4096, 4 * need));
+    if ((int64_t)B.lexrows.n < mcap * tau) B.lexrows.alloc(mcap * tau, s);
     NURI_CUDA(cudaMemsetAsync(B.lexcnt.p, 0, 8, s));
     k_rows_sorted<<<std::max(1, std::min<int>((int)((rc + 7) / 8), sm_count() * 16)), 256, 0, s>>>(
-        rs.buf.p, rc, tau, cx.g.vert_of, B.lexrows.p, B.lexcnt.p, (int64_t)m);
+        rs.buf.p, rc, tau, cx.g.vert_of, B.lexrows.p, B.lexcnt.p, mcap);
     NURI_CUDA(cudaGetLastError());
-    std::vector<int32_t> rows((size_t)m * tau);
-    NURI_CUDA(cudaMemcpyAsync(rows.data(), B.lexrows.p, sizeof(int32_t) * m * tau,
+    std::vector<int32_t> rows((size_t)mcap * tau);
+    NURI_CUDA(cudaMemcpyAsync(rows.data(), B.lexrows.p, sizeof(int32_t) * mcap * tau,
                               cudaMemcpyDeviceToHost, s));
     NURI_CUDA(cudaStreamSynchronize(s));
-    std::vector<int64_t> order(m);
-    for (int64_t i = 0; i < (int64_t)m; ++i) order[i] = i;
+    std::vector<int64_t> order(mcap);
+    for (int64_t i = 0; i < mcap; ++i) order[i] = i;
     std::nth_element(order.begin(), order.begin() + (need - 1), order.end(),
                      [&](int64_t a, int64_t b) {
                        return std::lexicographical_compare(
@@ -2307,7 +2357,7 @@ int64_t run_dense(Ctx cx, const Rec* recs, int64_t nrec, int grid, size_t dyn, D
         ws.q_cap = cap;
         in_is_a = true;
       }
-      compact_results(cx, rs, s);
+      compact_results(cx, rs, s, ws.lexL, ws.lex_tau);
       if (B.lex_allowed) update_lex<W>(cx, ws, rs, B, s);
       int32_t err = 0;
       NURI_CUDA(cudaMemcpyAsync(&err, &cx.st->err, 4, cudaMemcpyDeviceToHost, s));
