@@ -87,7 +87,8 @@ typedef struct nuri_stats {
   int32_t pad;
   double device_ms;        /* device time from first to last kernel of the query  */
   int64_t launches;        /* kernels of this library launched by the query       */
-  int64_t expand_launches; /* launches of the expansion kernel                    */
+  int64_t expand_launches; /* launches of the expansion kernel (cliques: also its
+                              dense-record launches)                              */
   double expand_ms;        /* summed device time of those launches (CUDA events)  */
   int64_t tail_launches;   /* cliques: launches of the dense-record task kernel    */
   double tail_ms;          /* cliques: summed device time of those launches        */
@@ -186,8 +187,9 @@ nuri_status nuri_topk_iso(nuri_graph* g, const nuri_query* q, int32_t k, int32_t
                           uint32_t flags, void* stream, nuri_result** out);
 
 /*
- * nuri_topk_iso_batch -- nq_batch isomorphism queries in one call; the seeds and frontiers of
+ * nuri_topk_iso_batch -- nqueries isomorphism queries in one call; the seeds and frontiers of
  * all queries are expanded together by the same kernels.  outs[i] receives query i's result.
+ * At most 4095 queries a call (NURI_ERR_LIMIT above).
  */
 nuri_status nuri_topk_iso_batch(nuri_graph* g, int32_t nqueries, const nuri_query* qs,
                                 const int32_t* ks, int32_t rank, uint32_t flags, void* stream,

@@ -1084,25 +1084,33 @@ __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
           __syncwarp();
         }
         if (in_core) {
+          // each lane owns whole rows: candidate i's bits against every candidate j (the
+          // loads of one row are independent and cached), the row built in registers
           const int cw = g.core_n >> 6;
-          const int nch = (p + 31) >> 5;
-          for (int t = 0; t < p * nch; ++t) {
-            const int i = t / nch, j = ((t - i * nch) << 5) + lane;
-            bool hit = false;
-            if (j < p && j != i) {
-              const int x = sp[j] - g.core_base;
-              hit = (__ldg(g.core_bits + (int64_t)(sp[i] - g.core_base) * cw + (x >> 6)) >>
-                     (x & 63)) & 1ull;
-            }
+          for (int i = lane; i < p; i += 32) {
+            const unsigned long long* crow =
+                g.core_bits + (int64_t)(sp[i] - g.core_base) * cw;
             if (pass == 0) {
-              const unsigned b = __ballot_sync(FULL, hit);
-              if (lane == 0 && b) dg[i] += __popc(b);
-            } else if (hit) {
-              const int a = inv[i], c = inv[j];
-              atomicOr(rows + a * W + (c >> 6), 1ull << (c & 63));
+              int d = 0;
+              for (int j = 0; j < p; ++j) {
+                const int x = sp[j] - g.core_base;
+                d += (j != i && ((__ldg(crow + (x >> 6)) >> (x & 63)) & 1ull)) ? 1 : 0;
+              }
+              dg[i] = d;
+            } else {
+              unsigned long long r[W];
+#pragma unroll
+              for (int q = 0; q < W; ++q) r[q] = 0ull;
+              for (int j = 0; j < p; ++j) {
+                const int x = sp[j] - g.core_base;
+                if (j != i && ((__ldg(crow + (x >> 6)) >> (x & 63)) & 1ull)) set_bit<W>(r, inv[j]);
+              }
+              const int a = inv[i];
+#pragma unroll
+              for (int q = 0; q < W; ++q) rows[a * W + q] = r[q];
             }
           }
-          if (lane == 0) my_bytes += 4ull * (unsigned long long)p * nch;
+          if (lane == 0) my_bytes += 4ull * (unsigned long long)p * ((p + 31) >> 5);
         }
         for (int i = 0; i < p && !in_core; ++i) {
           int32_t v = sp[i];
@@ -1684,9 +1692,10 @@ __device__ __forceinline__ bool adjacent_rank(const DevGraph& g, int32_t a, int3
 }
 
 // Warm start for tau (all-cliques ranking): one warp per seed grows a clique greedily inside
-// the seed's candidates (always adding the candidate with the most neighbours among the
-// remaining candidates when at most 64 remain, else the one of largest graph degree -- ties:
-// larger graph degree, then lower rank -- then keeping the candidates adjacent to it) and publishes subset_tau of its size.  The cliques themselves
+// the seed's candidates (narrow seeds, at most 64 candidates: in the order of their number of
+// neighbours among the candidates, computed once -- ties: larger graph degree, then lower
+// rank -- each one adjacent to all added before; wide seeds: always the remaining candidate
+// of largest graph degree, then keeping the candidates adjacent to it) and publishes subset_tau of its size.  The cliques themselves
 // are not recorded (the search finds them again); only the lower bound on the k-th best is
 // used, so the answer is unchanged.  buf: max_out entries per warp.
 __global__ void k_greedy_tau(DevGraph g, const int32_t* __restrict__ seeds, int64_t nseeds,
@@ -1703,16 +1712,60 @@ __global__ void k_greedy_tau(DevGraph g, const int32_t* __restrict__ seeds, int6
     for (int t = lane; t < p; t += 32) P[t] = g.oout[b + t];
     __syncwarp();
     int c = 1;
+    if (p <= 64) {
+      // narrow: candidates ordered once by (neighbours among the candidates, graph degree,
+      // -rank); a 64-bit mask keeps the ones adjacent to every candidate added so far
+      long long key[2] = {-1, -1};
+      for (int h = 0; h < 2; ++h) {
+        const int t = lane + 32 * h;
+        if (t >= p) continue;
+        const int32_t x = P[t];
+        int inner = 0;
+        for (int u = 0; u < p; ++u) inner += (u != t && adjacent_rank(g, x, P[u])) ? 1 : 0;
+        const int32_t d = min(__ldg(g.deg + __ldg(g.vert_of + x)), 0xFFFFF);
+        key[h] = ((long long)inner << 40) | ((long long)d << 20) |
+                 (long long)(0xFFFFF - (x & 0xFFFFF));
+      }
+      unsigned long long alive = p == 64 ? ~0ull : ((1ull << p) - 1);
+      while (alive) {
+        long long bk = -1;
+        int bt = -1;
+        for (int h = 0; h < 2; ++h) {
+          const int t = lane + 32 * h;
+          if (((alive >> t) & 1ull) && key[h] > bk) {
+            bk = key[h];
+            bt = t;
+          }
+        }
+        for (int o = 16; o; o >>= 1) {
+          const long long ok = __shfl_xor_sync(FULL, bk, o);
+          const int ot = __shfl_xor_sync(FULL, bt, o);
+          if (ok > bk || (ok == bk && ot >= 0 && (bt < 0 || ot < bt))) {
+            bk = ok;
+            bt = ot;
+          }
+        }
+        ++c;
+        const int32_t u = P[bt];
+        alive &= ~(1ull << bt);
+        bool keep[2] = {false, false};
+        for (int h = 0; h < 2; ++h) {
+          const int t = lane + 32 * h;
+          if ((alive >> t) & 1ull) keep[h] = adjacent_rank(g, P[t], u);
+        }
+        alive = (unsigned long long)__ballot_sync(FULL, keep[0]) |
+                ((unsigned long long)__ballot_sync(FULL, keep[1]) << 32);
+      }
+      p = 0;
+    }
     while (p > 0) {
-      // the candidate with the most neighbours among the candidates; key = (that count,
-      // graph degree, -rank), compared as one 64-bit value
+      // wide: the candidate of largest graph degree (ties: lowest rank), compared as one
+      // 64-bit key
       long long bestkey = -1;
       int best = -1;
       for (int t = lane; t < p; t += 32) {
         const int32_t x = P[t];
-        int inner = 0;
-        if (p <= 64)  // narrow candidate sets only: p^2 adjacency tests a step
-          for (int u = 0; u < p; ++u) inner += (u != t && adjacent_rank(g, x, P[u])) ? 1 : 0;
+        const int inner = 0;
         const int32_t d = min(__ldg(g.deg + __ldg(g.vert_of + x)), 0xFFFFF);
         const long long key = ((long long)inner << 40) | ((long long)d << 20) |
                               (long long)(0xFFFFF - (x & 0xFFFFF));
@@ -2203,17 +2256,24 @@ __global__ void k_lex_low(WideStore ws, int64_t nslots, const int32_t* __restric
 }
 
 // Device time and launches of the task kernel (CUDA events around every wave).
+// Also the dense-record launches of the expansion kernel (rec_*: k_clique_expand<2/4/8>).
 struct TailTime {
   double ms = 0.0;
   int64_t launches = 0;
-  cudaEvent_t a = nullptr, b = nullptr;
+  double rec_ms = 0.0;
+  int64_t rec_launches = 0;
+  cudaEvent_t a = nullptr, b = nullptr, c = nullptr, d = nullptr;
   TailTime() {
     cudaEventCreate(&a);
     cudaEventCreate(&b);
+    cudaEventCreate(&c);
+    cudaEventCreate(&d);
   }
   ~TailTime() {
     cudaEventDestroy(a);
     cudaEventDestroy(b);
+    cudaEventDestroy(c);
+    cudaEventDestroy(d);
   }
 };
 
@@ -2325,15 +2385,25 @@ int64_t run_dense(Ctx cx, const Rec* recs, int64_t nrec, int grid, size_t dyn, D
     WideStore ws = make_store(B, W, cn, s);
     NURI_CUDA(cudaMemsetAsync(B.counters.p, 0, 3 * sizeof(unsigned long long), s));
     NURI_CUDA(cudaMemsetAsync(&cx.st->work_next, 0, sizeof(int64_t), s));
+    NURI_CUDA(cudaEventRecord(tt.c, s));
     k_clique_expand<W><<<grid, KCfg<W>::WARPS * 32, dyn, s>>>(cx, recs + c0, nullptr, cn, ws);
     NURI_CUDA(cudaGetLastError());
+    NURI_CUDA(cudaEventRecord(tt.d, s));
     ++launched;
     bool in_is_a = true;  // the record kernel wrote its tasks to qa
     bool timed = false;   // a wave's events are pending
+    bool rec_timed = true;
     while (true) {
       unsigned long long cnt = 0;
       NURI_CUDA(cudaMemcpyAsync(&cnt, B.counters.p + 1, 8, cudaMemcpyDeviceToHost, s));
       NURI_CUDA(cudaStreamSynchronize(s));
+      if (rec_timed) {
+        float ms = 0.f;
+        NURI_CUDA(cudaEventElapsedTime(&ms, tt.c, tt.d));
+        tt.rec_ms += ms;
+        ++tt.rec_launches;
+        rec_timed = false;
+      }
       if (timed) {
         float ms = 0.f;
         NURI_CUDA(cudaEventElapsedTime(&ms, tt.a, tt.b));
@@ -2638,6 +2708,8 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
     rs.cap = res_cap;
     tail.ms = 0.0;
     tail.launches = 0;
+    tail.rec_ms = 0.0;
+    tail.rec_launches = 0;
     memset(&hs, 0, sizeof(hs));
     hs.tau = tau_init;
     NURI_CUDA(cudaMemcpyAsync(st.p, &hs, sizeof(hs), cudaMemcpyHostToDevice, s));
@@ -2999,6 +3071,8 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
   stats.dequeued += (int64_t)hs.dequeued;
   stats.adj_bytes += (int64_t)hs.adj_bytes;
   stats.tail_words = (int64_t)hs.tail_words;
+  stats.expand_ms += tail.rec_ms;  // the dense-record launches of the expansion kernel
+  stats.expand_launches += tail.rec_launches;
   stats.lex_pruned = (int64_t)hs.lex_pruned;
   stats.tail_ms = tail.ms;
   stats.tail_launches = tail.launches;

@@ -183,6 +183,64 @@ __global__ void k_iso_seeds(IsoCtx cx, int32_t q, int64_t base, int64_t count, i
   }
 }
 
+// Items of the search: a seed (query q, root image v) whose first-level candidate list (the
+// root's segment for the label of query position 1) is long is split into chunks of
+// kSeedChunk candidates, one item each, so that a hub root does not leave one warp working
+// long after the others (the search is tail-bound otherwise).  Every match is found once,
+// in the chunk holding its position-1 image.  An item's key is a bound for its chunk: the
+// root's score, the chunk's first (largest) candidate score, and the index bound of the
+// positions after 1.  Encoding: q << kItemQShift | chunk << 31 | v.
+constexpr int kSeedChunk = 64;
+constexpr int kItemQShift = 52;
+constexpr unsigned long long kItemChunkMask = (1ull << (kItemQShift - 31)) - 1;
+
+__global__ void k_iso_chunk_count(IsoCtx cx, const long long* __restrict__ keys,
+                                  const unsigned long long* __restrict__ vals, int64_t n,
+                                  int64_t* __restrict__ cnt) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(vals[i] >> 32);
+    const int32_t v = (int32_t)(uint32_t)vals[i];
+    const IsoQuery& Q = cx.qs[q];
+    int64_t c = 1;
+    if (keys[i] != NONE && Q.nq > 1) {
+      const int64_t so = (int64_t)v * cx.g.L + Q.lab[1];
+      const int64_t len = cx.g.lsoff[so + 1] - cx.g.lsoff[so];
+      c = len > kSeedChunk ? (len + kSeedChunk - 1) / kSeedChunk : 1;
+      if (c > (int64_t)kItemChunkMask + 1) c = (int64_t)kItemChunkMask + 1;  // unreachable
+    }
+    cnt[i] = c;
+  }
+}
+
+__global__ void k_iso_chunk_write(IsoCtx cx, const long long* __restrict__ keys,
+                                  const unsigned long long* __restrict__ vals, int64_t n,
+                                  const int64_t* __restrict__ off, long long* __restrict__ okeys,
+                                  unsigned long long* __restrict__ ovals) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long q = vals[i] >> 32;
+    const int32_t v = (int32_t)(uint32_t)vals[i];
+    const IsoQuery& Q = cx.qs[q];
+    const int64_t o = off[i], c = off[i + 1] - off[i];
+    for (int64_t j = 0; j < c; ++j) {
+      long long key = keys[i];
+      if (key != NONE && Q.nq > 1) {
+        const int64_t so = (int64_t)v * cx.g.L + Q.lab[1];
+        const int64_t at = cx.g.lsoff[so] + j * kSeedChunk;
+        if (at < cx.g.lsoff[so + 1]) {
+          // replace position 1's index bound by the chunk's largest candidate score
+          key = key - index_value(cx, v, Q.hop[1], Q.lab[1]) + (long long)__ldg(cx.seg + at).y;
+        } else {
+          key = NONE;  // an empty segment: the item finds nothing
+        }
+      }
+      okeys[o + j] = key;
+      ovals[o + j] = (q << kItemQShift) | ((unsigned long long)j << 31) | (unsigned)v;
+    }
+  }
+}
+
 // Raise query q's threshold to at least v (published by another part of a partitioned run).
 __global__ void k_iso_raise_tau(IsoState* st, int32_t q, long long v) {
   if (threadIdx.x == 0 && blockIdx.x == 0) atomicMax(&st[q].tau, v);
@@ -236,8 +294,9 @@ __global__ void __launch_bounds__(ISO_WARPS * 32) k_iso_search(IsoCtx cx,
     if (item >= nitems) break;
     long long bound = keys[item];
     unsigned long long pv = vals[item];
-    int q = (int)(pv >> 32);
-    int32_t v = (int32_t)(uint32_t)pv;
+    int q = (int)(pv >> kItemQShift);
+    int32_t v = (int32_t)(pv & 0x7FFFFFFFull);
+    const int64_t chunk = (int64_t)((pv >> 31) & kItemChunkMask);
     IsoState* S = cx.st + q;
     long long tau = ld_volatile64(&S->tau);
     if (bound == NONE || bound < tau) {
@@ -270,10 +329,11 @@ __global__ void __launch_bounds__(ISO_WARPS * 32) k_iso_search(IsoCtx cx,
     unsigned mask[QMAX];
     int lev = 1;
     {
+      // this item's chunk of the first level's candidates (the root's label segment)
       int32_t a = mu[Q.ppos[1]];
       int64_t so = (int64_t)a * g.L + Q.lab[1];
-      pos[1] = g.lsoff[so];
-      end[1] = g.lsoff[so + 1];
+      pos[1] = g.lsoff[so] + chunk * kSeedChunk;
+      end[1] = min(g.lsoff[so + 1], pos[1] + (int64_t)kSeedChunk);
       mask[1] = 0;
     }
     unsigned steps = 0;
@@ -630,8 +690,10 @@ bool prepare_query(const nuri_query& in, int32_t k, const std::vector<int32_t>& 
 // state, its result region and the final selection and merge over that region.
 int64_t iso_query_bytes(const nuri_graph* G, int32_t k) {
   const int64_t seeds = std::max<int64_t>(G->d.n, 1);
+  const int64_t chunks = seeds + G->d.nnz / kSeedChunk;  // seeds split into first-level chunks
   const int64_t cap = std::max<int64_t>(16384, (int64_t)k * 64);
-  return seeds * (4 * 8 + 16) + (int64_t)NBINS * 4 + (int64_t)sizeof(IsoState) +
+  return seeds * (2 * 8 + 2 * 8 + 16) + chunks * (4 * 8 + 16) + (int64_t)NBINS * 4 +
+         (int64_t)sizeof(IsoState) +
          (int64_t)sizeof(IsoQuery) +
          cap * ((int64_t)sizeof(IsoRes) + 4 + 8 + 4 * KCOLS + 4 * 4 + 8 * 2);
 }
@@ -644,6 +706,9 @@ void topk_iso_batch(nuri_graph* G, int32_t nqueries, const nuri_query* qs, const
   const bool keep_ties = flags & NURI_KEEP_TIES;
   const std::vector<int32_t>& gmax = deg ? G->h_gmax_d : G->h_gmax_w;
   int64_t launches = 0;
+  if (nqueries >= (1 << (64 - kItemQShift)))
+    NURI_FAIL(NURI_ERR_LIMIT, "nuri_topk_iso: at most %d queries in one batch",
+              (1 << (64 - kItemQShift)) - 1);
   std::vector<Prepared> prep(nqueries);
   for (int i = 0; i < nqueries; ++i)
     if (!prepare_query(qs[i], ks[i], gmax, g.L, (flags & NURI_ISO_INDUCED) != 0, &prep[i]))
@@ -690,6 +755,34 @@ void topk_iso_batch(nuri_graph* G, int32_t nqueries, const nuri_query* qs, const
     }
   }
   if (nitems > 0) {
+    // split long first levels into chunks (see k_iso_chunk_count)
+    DBuf<int64_t> ccnt, coff;
+    ccnt.alloc(nitems + 1, s);
+    coff.alloc(nitems + 1, s);
+    NURI_CUDA(cudaMemsetAsync(ccnt.p + nitems, 0, sizeof(int64_t), s));
+    ++launches;
+    k_iso_chunk_count<<<gridn(nitems), 256, 0, s>>>(cx, keys.p, vals.p, nitems, ccnt.p);
+    size_t tbs = 0;
+    cub::DeviceScan::ExclusiveSum(nullptr, tbs, ccnt.p, coff.p, nitems + 1, s);
+    DBuf<uint8_t> stmp;
+    stmp.alloc(tbs, s);
+    NURI_CUDA(cub::DeviceScan::ExclusiveSum(stmp.p, tbs, ccnt.p, coff.p, nitems + 1, s));
+    int64_t nchunks = 0;
+    NURI_CUDA(cudaMemcpyAsync(&nchunks, coff.p + nitems, 8, cudaMemcpyDeviceToHost, s));
+    NURI_CUDA(cudaStreamSynchronize(s));
+    DBuf<long long> ckeys;
+    DBuf<unsigned long long> cvals;
+    ckeys.alloc(std::max<int64_t>(nchunks, 1), s);
+    cvals.alloc(std::max<int64_t>(nchunks, 1), s);
+    ++launches;
+    k_iso_chunk_write<<<gridn(nitems), 256, 0, s>>>(cx, keys.p, vals.p, nitems, coff.p, ckeys.p,
+                                                   cvals.p);
+    NURI_CUDA(cudaGetLastError());
+    nitems = nchunks;
+    keys = std::move(ckeys);
+    vals = std::move(cvals);
+    keys2.alloc(std::max<int64_t>(nitems, 1), s);
+    vals2.alloc(std::max<int64_t>(nitems, 1), s);
     size_t tb = 0;
     cub::DeviceRadixSort::SortPairsDescending(nullptr, tb, keys.p, keys2.p, vals.p, vals2.p, nitems, 0, 64, s);
     DBuf<uint8_t> tmp;

@@ -25,3 +25,18 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+@pytest.fixture(autouse=True)
+def _query_time_budget(request):
+    """Every query of a GPU test runs under a device time budget: a search that ran away
+    fails its test with NURI_ERR_TIMEOUT (the message names the rounds and nodes it reached)
+    instead of holding the run."""
+    if "gpu" not in request.keywords:
+        yield
+        return
+    import paper_1807_08888_b300 as nuri
+    nuri.set_time_budget(120000.0)
+    yield
+    nuri.set_time_budget(0.0)
+
