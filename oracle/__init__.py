@@ -64,8 +64,8 @@ def lib():
             L.orc_topk_cliques.argtypes = [i32, i64, P, P, i32, i32, i64, RP]
             L.orc_bk_cliques.argtypes = [i32, i64, P, P, i32, i32, RP]
             L.orc_hop_index.argtypes = [i32, i64, P, P, P, P, i32, i32, i32, P]
-            L.orc_topk_iso.argtypes = [i32, i64, P, P, P, P, i32, i32, P, i32, P, P, i32, i64,
-                                       i32, RP]
+            L.orc_topk_iso.argtypes = [i32, i64, P, P, P, P, P, i32, i32, P, i32, P, P, i32,
+                                       i64, i32, RP]
             L.orc_mni.argtypes = [i32, i64, P, P, P, i32, P, i32, P, P, P, P]
             L.orc_topk_patterns.argtypes = [i32, i64, P, P, P, i32, i32, RP]
             L.orc_canonical_code.argtypes = [i32, P, i32, P, P, P, P]
@@ -142,16 +142,19 @@ def hop_index(g, num_labels: int, hops: int, method: int = 1) -> np.ndarray:
 
 
 def topk_iso(g, q, k: int, degree_rank: bool = False, budget: int = 0,
-             induced: bool = False) -> Result:
+             induced: bool = False, edge_rank: bool = False) -> Result:
     """Algorithm 1 with the subgraph-isomorphism functions of Section 4.3 (induced: the
-    images of non-adjacent query vertices must be non-adjacent too)."""
+    images of non-adjacent query vertices must be non-adjacent too; edge_rank: scores are
+    sums of ``g.edge_weights`` over the image's edges, Section 2's cumulative edge weight)."""
     s, d = _edges(g)
     lab = np.ascontiguousarray(g.labels, dtype=np.uint8)
     w = None if g.weights is None else np.ascontiguousarray(g.weights, dtype=np.int32)
+    ew = None if g.edge_weights is None else np.ascontiguousarray(g.edge_weights, dtype=np.int32)
+    rank = 2 if edge_rank else (1 if degree_rank else 0)
     ql, qs, qd = q.as_arrays()
     rp = ctypes.POINTER(_Res)()
-    rc = lib().orc_topk_iso(g.n, s.size, _ptr(s), _ptr(d), _ptr(lab), _ptr(w),
-                            int(degree_rank), q.nq, _ptr(ql), qs.size, _ptr(qs), _ptr(qd), k,
+    rc = lib().orc_topk_iso(g.n, s.size, _ptr(s), _ptr(d), _ptr(lab), _ptr(w), _ptr(ew),
+                            rank, q.nq, _ptr(ql), qs.size, _ptr(qs), _ptr(qd), k,
                             budget, int(induced), ctypes.byref(rp))
     if rc:
         raise ValueError("orc_topk_iso rc=%d" % rc)

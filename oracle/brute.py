@@ -7,7 +7,7 @@ Used to pin the Algorithm 1 / Algorithm 2 oracle (``nuri_oracle.cpp``) on small 
   score = size; CLIQUE_MAXIMAL keeps the ones no vertex can extend.
 * subgraph isomorphism: every injective label-preserving map of the query whose query edges
   land on data edges (Section 2 "Subgraph Isomorphism", non-induced reading); a result is the
-  image (V_s, E_s); score = sum of vertex scores.
+  image (V_s, E_s); score = sum of vertex scores, or of edge weights over E_s.
 * patterns: every connected M-edge subset of E defines a pattern (its image graph); a
   pattern's domains come from every injective map of the pattern into G; f = min domain size
   (Section 2, minimum image-based support).
@@ -51,13 +51,28 @@ def topk_cliques(g, k, maximal=False):
     return [(len(c), c) for c in cl[:k]]
 
 
-def iso_images(g, q, degree_rank=False, induced=False):
+def edge_weight_map(g):
+    """Weight of each undirected edge {a, b} (a < b): the largest weight of its input pairs."""
+    w = {}
+    for a, b, x in zip(g.src.tolist(), g.dst.tolist(), g.edge_weights.tolist()):
+        if a != b:
+            e = (min(a, b), max(a, b))
+            w[e] = max(w.get(e, x), x)
+    return w
+
+
+def iso_images(g, q, degree_rank=False, induced=False, edge_rank=False):
     """All distinct images (V_s, E_s) of matches, with their scores: non-induced (query
     edges land on data edges), or induced (also: non-adjacent query vertices land on
-    non-adjacent data vertices)."""
+    non-adjacent data vertices).  Scores: sum of vertex weights or degrees over V_s, or
+    (edge_rank) sum of edge weights over E_s."""
     adj = clean_adj(g)
     lab = g.labels.tolist()
-    score = [len(adj[v]) for v in range(g.n)] if degree_rank else g.weights.tolist()
+    ew = edge_weight_map(g) if edge_rank else None
+    if edge_rank:
+        score = None
+    else:
+        score = [len(adj[v]) for v in range(g.n)] if degree_rank else g.weights.tolist()
     cands = [[v for v in range(g.n) if lab[v] == q.labels[i]] for i in range(q.nq)]
     images = {}
     for mp in itertools.product(*cands):
@@ -71,12 +86,12 @@ def iso_images(g, q, degree_rank=False, induced=False):
                     continue
             V = tuple(sorted(mp))
             E = tuple(sorted((min(mp[a], mp[b]), max(mp[a], mp[b])) for a, b in q.edges))
-            images[(V, E)] = sum(score[v] for v in mp)
+            images[(V, E)] = sum(ew[e] for e in E) if edge_rank else sum(score[v] for v in mp)
     return images
 
 
-def topk_iso(g, q, k, degree_rank=False, induced=False):
-    im = iso_images(g, q, degree_rank, induced)
+def topk_iso(g, q, k, degree_rank=False, induced=False, edge_rank=False):
+    im = iso_images(g, q, degree_rank, induced, edge_rank)
     rows = sorted(((s, V, E) for (V, E), s in im.items()), key=lambda r: (-r[0], r[1], r[2]))
     return rows[:k]
 

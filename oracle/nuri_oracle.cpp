@@ -538,26 +538,55 @@ extern "C" int orc_hop_index(int32_t n, int64_t m, const int32_t* src, const int
 //   subgraph isomorphic to the matched part of the query -- Ullmann-style targeted expansion).
 //   score = sum of vertex scores (weights, or degrees when rank == 1);
 //   u = sum over unmatched q of index(mu(root), label(q), hop(q));
+//   rank == 2 ranks by the other criterion that Section 2's top-k semantics names, the
+//   cumulative edge weight: score = sum of w(e) over the image's edges E_s (the data edges the
+//   query edges land on), u = (query edges not yet matched) x (largest edge weight), a valid
+//   bound since every unmatched query edge adds one data edge of weight at most that.
+//   Edge weights ew[e] belong to the input pair (src[e], dst[e]); an undirected edge given by
+//   several pairs takes the largest of their weights; pairs without a weight of their own do
+//   not exist (every pair carries one).
 //   priority = (matched query edges, score + u);  dominated(s, o) = score + u < score(o);
 //   relevant(s) = every query vertex is matched.  Automorphic mappings with the same image are
 //   one subgraph: an image already in R is not inserted again.
-// rank: 0 = weight sum, 1 = degree sum.  H_avail: number of index hops to use (>= query radius
+// rank: 0 = weight sum, 1 = degree sum, 2 = edge-weight sum.  H_avail: number of index hops to use (>= query radius
 // is exact; hops beyond it use the per-label global maximum, which is also a valid bound).
 // induced != 0: the other reading of Section 2's definition (an edge between two images iff
 // there is one between the query vertices): expandable() also rejects an image adjacent to the
 // image of an already-matched query vertex that is not adjacent to the new one.
 // =============================================================================================
 extern "C" int orc_topk_iso(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
-                            const uint8_t* labels, const int32_t* weights, int32_t rank,
+                            const uint8_t* labels, const int32_t* weights,
+                            const int32_t* edge_w, int32_t rank,
                             int32_t nq, const uint8_t* qlab, int32_t qne, const int32_t* qsrc,
                             const int32_t* qdst, int32_t k, int64_t budget, int32_t induced,
                             orc_result** out) {
   if (k < 1 || nq < 1 || nq > 8 || !labels) return 1;
   if (rank == 0 && !weights) return 1;
+  if (rank == 2 && !edge_w) return 1;
+  if (rank < 0 || rank > 2) return 1;
   double t0 = now_s();
   G g = build_graph(n, m, src, dst);
-  vector<int64_t> score_of(n);
-  for (int v = 0; v < n; ++v) score_of[v] = rank == 1 ? (int64_t)g.adj[v].size() : weights[v];
+  vector<int64_t> score_of(n, 0);
+  if (rank != 2)
+    for (int v = 0; v < n; ++v) score_of[v] = rank == 1 ? (int64_t)g.adj[v].size() : weights[v];
+  // edge weights (rank 2): the largest weight given for each undirected edge
+  std::map<std::pair<int, int>, int64_t> wedge;
+  int64_t wmax = 0;
+  if (rank == 2)
+    for (int64_t e = 0; e < m; ++e) {
+      const int a = src[e], b = dst[e];
+      if (a == b) continue;
+      if (edge_w[e] < 0) return 1;
+      auto key = std::make_pair(std::min(a, b), std::max(a, b));
+      auto it = wedge.find(key);
+      if (it == wedge.end()) wedge[key] = edge_w[e];
+      else it->second = std::max(it->second, (int64_t)edge_w[e]);
+      wmax = std::max(wmax, (int64_t)edge_w[e]);
+    }
+  auto wof = [&](int a, int b) -> int64_t {
+    return wedge.at(std::make_pair(std::min(a, b), std::max(a, b)));
+  };
+  int qedges = 0;
   // query adjacency
   vector<vector<int>> qadj(nq, vector<int>(nq, 0));
   for (int e = 0; e < qne; ++e) {
@@ -565,6 +594,8 @@ extern "C" int orc_topk_iso(int32_t n, int64_t m, const int32_t* src, const int3
     if (a < 0 || b < 0 || a >= nq || b >= nq || a == b) return 1;
     qadj[a][b] = qadj[b][a] = 1;
   }
+  for (int a = 0; a < nq; ++a)
+    for (int b = a + 1; b < nq; ++b) qedges += qadj[a][b];
   auto bfs = [&](int r, vector<int>& dist, vector<int>& order, vector<int>& par) {
     dist.assign(nq, -1);
     par.assign(nq, -1);
@@ -615,7 +646,14 @@ extern "C" int orc_topk_iso(int32_t n, int64_t m, const int32_t* src, const int3
     int map[8];
     int64_t score, bound;
   };
+  auto edges_matched = [&](int depth) {
+    int c = 0;
+    for (int i = 0; i < depth; ++i)
+      for (int j = i + 1; j < depth; ++j) c += qadj[order[i]][order[j]];
+    return c;
+  };
   auto upper = [&](const IsoSub& s) -> int64_t {
+    if (rank == 2) return s.score + (int64_t)(qedges - edges_matched(s.depth)) * wmax;
     int64_t u = 0;
     for (int i = s.depth; i < nq; ++i) {
       int q = order[i];
@@ -624,12 +662,6 @@ extern "C" int orc_topk_iso(int32_t n, int64_t m, const int32_t* src, const int3
       u += v;
     }
     return s.score + u;
-  };
-  auto edges_matched = [&](int depth) {
-    int c = 0;
-    for (int i = 0; i < depth; ++i)
-      for (int j = i + 1; j < depth; ++j) c += qadj[order[i]][order[j]];
-    return c;
   };
   struct QE {
     int64_t p0, p1, seq;
@@ -714,6 +746,9 @@ extern "C" int orc_topk_iso(int32_t n, int64_t m, const int32_t* src, const int3
       c.map[c.depth] = x;
       c.depth += 1;
       c.score = s.score + score_of[x];
+      if (rank == 2)  // the query edges from q to the matched vertices land on these edges
+        for (int i = 0; i < s.depth; ++i)
+          if (qadj[q][order[i]]) c.score += wof(x, s.map[i]);
       c.bound = upper(c);
       ++expansions;
       if (!R.full() || !(c.bound < R.kth())) enqueue(c);

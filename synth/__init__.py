@@ -23,7 +23,7 @@ import numpy as np
 
 __all__ = [
     "Graph", "Query", "er_planted", "chung_lu_planted", "expected_degrees", "rmat", "labels_uniform",
-    "labels_zipf", "weights_uniform", "random_query", "query_batch", "er_small",
+    "labels_zipf", "weights_uniform", "edge_weights_uniform", "random_query", "query_batch", "er_small",
     "fixture_clique_example", "fixture_pattern_example", "path_query", "cycle_query",
     "star_query", "tree_query", "serving_requests", "workload",
 ]
@@ -39,6 +39,7 @@ class Graph:
     weights: np.ndarray | None = None  # int32 [n]
     planted: list = field(default_factory=list)  # planted cliques (sorted int lists)
     name: str = ""
+    edge_weights: np.ndarray | None = None  # int32 [m]: one weight per input pair
 
     @property
     def m(self) -> int:
@@ -53,6 +54,9 @@ class Graph:
             h.update(np.ascontiguousarray(self.labels, dtype=np.uint8).tobytes())
         if self.weights is not None:
             h.update(np.ascontiguousarray(self.weights, dtype=np.int32).tobytes())
+        if self.edge_weights is not None:
+            h.update(b"edge_weights")
+            h.update(np.ascontiguousarray(self.edge_weights, dtype=np.int32).tobytes())
         return h.hexdigest()
 
 
@@ -239,6 +243,11 @@ def labels_zipf(n: int, num_labels: int, s: float, seed: int) -> np.ndarray:
 def weights_uniform(n: int, lo: int, hi: int, seed: int) -> np.ndarray:
     """Integer weights uniform on the inclusive range [lo, hi]."""
     return np.random.default_rng(seed).integers(lo, hi + 1, size=n).astype(np.int32)
+
+
+def edge_weights_uniform(m: int, lo: int, hi: int, seed: int) -> np.ndarray:
+    """One int32 weight per input pair, uniform in [lo, hi]."""
+    return np.random.default_rng(seed).integers(lo, hi + 1, size=m).astype(np.int32)
 
 
 def path_query(labels) -> Query:

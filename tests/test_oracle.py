@@ -398,3 +398,55 @@ def test_iso_oracle_induced_vs_brute():
     q = synth.path_query([0, 0, 0])
     assert len(oracle.topk_iso(g, q, 10)) == 3
     assert len(oracle.topk_iso(g, q, 10, induced=True)) == 0
+
+
+def _with_edge_weights(g, rng, hi=25):
+    """One weight per input pair; a third of the pairs are given once more, reversed, with
+    a weight of their own (an edge then weighs the larger of the two)."""
+    if g.m:
+        pick = rng.integers(0, g.m, size=max(1, g.m // 3))
+        src = np.concatenate([g.src, g.dst[pick]]).astype(np.int32)
+        dst = np.concatenate([g.dst, g.src[pick]]).astype(np.int32)
+        g.src, g.dst = src, dst
+    g.edge_weights = rng.integers(0, hi + 1, size=g.m).astype(np.int32)
+    return g
+
+
+def test_iso_oracle_edge_rank_vs_brute():
+    """Ranking by cumulative edge weight (Section 2, top-k semantics: the matches of the
+    highest cumulative edge weight), pinned by brute force: every image scored by the sum of
+    its edges' weights, non-induced and induced, queries of 1 to 6 vertices."""
+    rng = np.random.default_rng(41)
+    for g in _tiny_labelled(50, seed0=1500, nlab=2):
+        g = _with_edge_weights(g, rng)
+        qs = _queries(rng, 2) + [synth.random_query(rng, "tree", 6, 2)]
+        for q in qs:
+            for k in (1, 4, 50):
+                for induced in (False, True):
+                    want = brute.topk_iso(g, q, k, induced=induced, edge_rank=True)
+                    got = [r[:3] for r in oracle.topk_iso(g, q, k, induced=induced,
+                                                          edge_rank=True)]
+                    assert got == want, (g.name, q, k, induced)
+
+
+def test_iso_oracle_edge_rank_worked_example():
+    """Two disjoint triangles: {0,1,2} with edge weights 1, 1, 1 and {3,4,5} with 5, 1, 1.
+    The heavier triangle wins (7 > 3) until the pair (1, 0) is given again with weight 9: an
+    edge weighs the largest weight given for it, so {0,1,2} then weighs 11."""
+    src = np.array([0, 1, 2, 3, 4, 5], np.int32)
+    dst = np.array([1, 2, 0, 4, 5, 3], np.int32)
+    w = np.array([1, 1, 1, 5, 1, 1], np.int32)
+    g = synth.Graph(6, src, dst, labels=np.zeros(6, np.uint8), weights=np.ones(6, np.int32),
+                    edge_weights=w)
+    tri = synth.cycle_query([0, 0, 0])
+    edge = synth.path_query([0, 0])
+    assert [r[:2] for r in oracle.topk_iso(g, tri, 2, edge_rank=True)] == [
+        (7, (3, 4, 5)), (3, (0, 1, 2))]
+    assert [r[:2] for r in oracle.topk_iso(g, edge, 3, edge_rank=True)] == [
+        (5, (3, 4)), (1, (0, 1)), (1, (0, 2))]
+    g2 = synth.Graph(6, np.append(src, 1).astype(np.int32), np.append(dst, 0).astype(np.int32),
+                     labels=g.labels, weights=g.weights,
+                     edge_weights=np.append(w, 9).astype(np.int32))
+    assert [r[:2] for r in oracle.topk_iso(g2, tri, 2, edge_rank=True)] == [
+        (11, (0, 1, 2)), (7, (3, 4, 5))]
+    assert oracle.topk_iso(g2, edge, 1, edge_rank=True)[0][:2] == (9, (0, 1))
