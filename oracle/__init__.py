@@ -63,6 +63,7 @@ def lib():
             L.orc_free.argtypes = [ctypes.POINTER(_Res)]
             L.orc_topk_cliques.argtypes = [i32, i64, P, P, i32, i32, i64, RP]
             L.orc_bk_cliques.argtypes = [i32, i64, P, P, i32, i32, RP]
+            L.orc_topk_wcliques.argtypes = [i32, i64, P, P, P, i32, i32, i64, RP]
             L.orc_hop_index.argtypes = [i32, i64, P, P, P, P, i32, i32, i32, P]
             L.orc_topk_iso.argtypes = [i32, i64, P, P, P, P, P, i32, i32, P, i32, P, P, i32,
                                        i64, i32, RP]
@@ -115,6 +116,19 @@ def topk_cliques(g, k: int, maximal: bool = False, budget: int = 0) -> Result:
                                 ctypes.byref(rp))
     if rc:
         raise ValueError("orc_topk_cliques rc=%d" % rc)
+    return _unpack(rp)
+
+
+def topk_wcliques(g, k: int, maximal: bool = False, budget: int = 0) -> Result:
+    """Algorithm 1 with the clique functions, ranked by the sum of ``g.weights`` over the
+    clique (Section 2's top-k semantics with a cumulative weight)."""
+    s, d = _edges(g)
+    w = np.ascontiguousarray(g.weights, dtype=np.int32)
+    rp = ctypes.POINTER(_Res)()
+    rc = lib().orc_topk_wcliques(g.n, s.size, _ptr(s), _ptr(d), _ptr(w), k, int(maximal),
+                                 budget, ctypes.byref(rp))
+    if rc:
+        raise ValueError("orc_topk_wcliques rc=%d" % rc)
     return _unpack(rp)
 
 

@@ -4,7 +4,8 @@ Pure Python, no pruning, no priorities: every object is enumerated and ranked af
 Used to pin the Algorithm 1 / Algorithm 2 oracle (``nuri_oracle.cpp``) on small inputs.
 
 * cliques: every non-empty pairwise-adjacent vertex set (Section 2 "Clique Discovery"),
-  score = size; CLIQUE_MAXIMAL keeps the ones no vertex can extend.
+  score = size (or the sum of vertex weights); CLIQUE_MAXIMAL keeps the ones no vertex can
+  extend.
 * subgraph isomorphism: every injective label-preserving map of the query whose query edges
   land on data edges (Section 2 "Subgraph Isomorphism", non-induced reading); a result is the
   image (V_s, E_s); score = sum of vertex scores, or of edge weights over E_s.
@@ -49,6 +50,18 @@ def topk_cliques(g, k, maximal=False):
               if not set.intersection(*[adj[v] for v in c]) - set(c)]
     cl.sort(key=lambda c: (-len(c), c))
     return [(len(c), c) for c in cl[:k]]
+
+
+def topk_wcliques(g, k, maximal=False):
+    """Every clique scored by the sum of its vertex weights; ties by sorted ids."""
+    adj = clean_adj(g)
+    w = g.weights.tolist()
+    cl = all_cliques(g)
+    if maximal:
+        cl = [c for c in cl
+              if not set.intersection(*[adj[v] for v in c]) - set(c)]
+    rows = sorted(((sum(w[v] for v in c), c) for c in cl), key=lambda r: (-r[0], r[1]))
+    return rows[:k]
 
 
 def edge_weight_map(g):

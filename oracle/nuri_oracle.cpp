@@ -12,6 +12,8 @@
 //   * orc_topk_cliques  -- Algorithm 1 (Section 3.2) with the clique user functions of
 //     Section 3.2 / Section 4.1 (Listing 1's candidate set P, the Carraghan-Pardalos bound,
 //     priority (|V|,|P|)), canonical extension by increasing id (Section 3.2 example).
+//   * orc_topk_wcliques -- the same with vertex-weighted ranking (Section 2 top-k semantics:
+//     a cumulative weight as the ranking criterion) and the weighted Carraghan-Pardalos bound.
 //   * orc_bk_cliques    -- Bron-Kerbosch with pivoting over a degeneracy order: an
 //     independent enumeration of maximal cliques used to pin orc_topk_cliques.
 //   * orc_hop_index     -- the hop/label max index of Section 4.3 (Listing 3), both by explicit
@@ -297,6 +299,122 @@ extern "C" int orc_topk_cliques(int32_t n, int64_t m, const int32_t* src, const 
           enqueue(std::move(c));                  // enqueue the child
         else
           ++pruned;
+      }
+    }
+    if (budget > 0 && expansions >= budget) {
+      complete = 0;
+      break;
+    }
+  }
+  vector<Row> rows;
+  for (auto& kv : R.by_score)
+    for (auto& V : kv.second) {
+      Row r;
+      r.score = kv.first;
+      r.verts = V;
+      rows.push_back(r);
+    }
+  std::sort(rows.begin(), rows.end(), [](const Row& a, const Row& b) {
+    if (a.score != b.score) return a.score > b.score;
+    return lex_less(a.verts, b.verts);
+  });
+  if ((int)rows.size() > k) rows.resize(k);
+  orc_result* r = pack(rows);
+  r->expansions = expansions;
+  r->dequeued = dequeued;
+  r->pruned = pruned;
+  r->complete = complete;
+  r->seconds = now_s() - t0;
+  *out = r;
+  return 0;
+}
+
+// =============================================================================================
+// Vertex-weighted cliques: Algorithm 1 with the clique user functions above, ranked by the
+// other criterion Section 2's top-k semantics allows, a cumulative weight: score(s) = sum of
+// w(v) over V_s (weights >= 0).  The bound follows the Carraghan-Pardalos one with weights:
+// every clique below s adds a subset of P_s, so dominated(s, o) = w(V_s) + w(P_s) < score(o).
+//   priority(s) = (w(V_s) + w(P_s), w(V_s))      (best bound first; it orders work only)
+// Ties at the k-th place are broken by sorted ids, as for sizes.
+// =============================================================================================
+extern "C" int orc_topk_wcliques(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                                 const int32_t* weights, int32_t k, int32_t maximal_only,
+                                 int64_t budget, orc_result** out) {
+  if (k < 1 || n < 0 || (n > 0 && !weights)) return 1;
+  for (int v = 0; v < n; ++v)
+    if (weights[v] < 0) return 1;
+  double t0 = now_s();
+  G g = build_graph(n, m, src, dst);
+  auto wsum = [&](const vector<int>& S) {
+    int64_t t = 0;
+    for (int v : S) t += weights[v];
+    return t;
+  };
+  struct QE {
+    int64_t p0, p1, seq;
+    int32_t idx;
+  };
+  struct Cmp {
+    bool operator()(const QE& a, const QE& b) const {
+      if (a.p0 != b.p0) return a.p0 < b.p0;
+      if (a.p1 != b.p1) return a.p1 < b.p1;
+      return a.seq > b.seq;
+    }
+  };
+  struct WSub {
+    CliqueSub s;
+    int64_t wv, wp;  // w(V_s), w(P_s)
+  };
+  vector<WSub> store;
+  vector<int32_t> free_slots;
+  std::priority_queue<QE, vector<QE>, Cmp> Q;
+  int64_t seq = 0;
+  auto enqueue = [&](WSub&& x) {
+    int32_t slot;
+    if (!free_slots.empty()) {
+      slot = free_slots.back();
+      free_slots.pop_back();
+      store[slot] = std::move(x);
+    } else {
+      slot = (int32_t)store.size();
+      store.push_back(std::move(x));
+    }
+    Q.push({store[slot].wv + store[slot].wp, store[slot].wv, seq++, slot});
+  };
+  for (int v = 0; v < n; ++v) {
+    WSub x;
+    x.s.V = {v};
+    for (int u : g.adj[v])
+      if (u > v) x.s.P.push_back(u);
+    x.wv = weights[v];
+    x.wp = wsum(x.s.P);
+    enqueue(std::move(x));
+  }
+  ResultSet<vector<int>> R(k);
+  int64_t expansions = 0, dequeued = 0, pruned = 0;
+  int complete = 1;
+  while (!Q.empty()) {
+    QE top = Q.top();
+    Q.pop();
+    WSub x = std::move(store[top.idx]);
+    free_slots.push_back(top.idx);
+    ++dequeued;
+    bool relevant = true;
+    if (maximal_only) relevant = common_nbrs_all(g, x.s.V).empty();
+    if (relevant) R.offer(x.wv, x.s.V);
+    if (!R.full() || !(x.wv + x.wp < R.kth())) {
+      for (size_t j = 0; j < x.s.P.size(); ++j) {
+        int d = x.s.P[j];
+        WSub c;
+        c.s.V = x.s.V;
+        c.s.V.push_back(d);
+        for (size_t t = j + 1; t < x.s.P.size(); ++t)
+          if (g.has(d, x.s.P[t])) c.s.P.push_back(x.s.P[t]);
+        c.wv = x.wv + weights[d];
+        c.wp = wsum(c.s.P);
+        ++expansions;
+        if (!R.full() || !(c.wv + c.wp < R.kth())) enqueue(std::move(c));
+        else ++pruned;
       }
     }
     if (budget > 0 && expansions >= budget) {

@@ -450,3 +450,29 @@ def test_iso_oracle_edge_rank_worked_example():
     assert [r[:2] for r in oracle.topk_iso(g2, tri, 2, edge_rank=True)] == [
         (11, (0, 1, 2)), (7, (3, 4, 5))]
     assert oracle.topk_iso(g2, edge, 1, edge_rank=True)[0][:2] == (9, (0, 1))
+
+
+def test_weighted_cliques_oracle_vs_brute():
+    """Cliques ranked by the sum of vertex weights (Algorithm 1 with the weighted bound
+    w(V) + w(P)), pinned by brute force on tiny graphs: all cliques and maximal ones."""
+    rng = np.random.default_rng(43)
+    for i in range(60):
+        n = int(rng.integers(1, 11))
+        g = synth.er_small(n, [0.3, 0.5, 0.8][i % 3], seed=1600 + i)
+        g.weights = rng.integers(0, [3, 50][i % 2] + 1, size=n).astype(np.int32)
+        for k in (1, 3, 10, 1000):
+            for maximal in (False, True):
+                want = [(s, tuple(c)) for s, c in brute.topk_wcliques(g, k, maximal)]
+                got = [(r[0], tuple(r[1])) for r in oracle.topk_wcliques(g, k, maximal)]
+                assert got == want, (g.name, k, maximal)
+
+
+def test_weighted_cliques_unit_weights_rank_by_size():
+    """With every weight 1 the weighted ranking is the ranking by size (Algorithm 1 with the
+    unweighted functions), on graphs beyond brute force."""
+    for seed in (3, 4):
+        g = synth.rmat(9, 8, seed=seed)
+        g.weights = np.ones(g.n, np.int32)
+        for k in (1, 30, 300):
+            want = [(r[0], tuple(r[1])) for r in oracle.topk_cliques(g, k)]
+            assert [(r[0], tuple(r[1])) for r in oracle.topk_wcliques(g, k)] == want
