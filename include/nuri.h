@@ -50,9 +50,11 @@ typedef int32_t nuri_status;
 
 /* ranking functions */
 #define NURI_RANK_SIZE 0        /* cliques: |V_s|                                           */
-#define NURI_RANK_WEIGHT_SUM 1  /* isomorphism: sum of the int32 vertex weights            */
+#define NURI_RANK_WEIGHT_SUM 1  /* isomorphism, cliques: sum of the int32 vertex weights   */
 #define NURI_RANK_DEGREE_SUM 2  /* isomorphism: sum of vertex degrees (the paper's Sec. 6.4) */
 #define NURI_RANK_MNI 3         /* patterns: minimum image-based support                   */
+#define NURI_RANK_EDGE_WEIGHT_SUM 4 /* isomorphism: sum of the int32 weights of the image's
+                                       edges (Section 2's cumulative edge weight)           */
 
 /* nuri_load_graph flags */
 #define NURI_LOAD_DEVICE_INPUT 0x1u /* src/dst/labels/weights are device pointers          */
@@ -134,7 +136,9 @@ typedef struct nuri_graph_info {
   int64_t num_edges;     /* undirected edges after clean-up */
   int64_t dropped;       /* input pairs dropped (self-loops and duplicates) */
   int32_t max_degree;
-  int32_t max_out_degree;/* in the degree orientation used for cliques */
+  int32_t max_out_degree;/* in the orientation used for cliques: the batch-peeling (core)
+                            order, where it equals the degeneracy, or the (degree, id)
+                            order when the peel would take over 20000 batches */
   int32_t index_hops;    /* hops of the hop/label index that is resident */
   int32_t pad;
   int64_t device_bytes;  /* device memory held by the graph */
@@ -161,11 +165,31 @@ void nuri_free_graph(nuri_graph* g);
 nuri_status nuri_graph_get_info(const nuri_graph* g, nuri_graph_info* info);
 
 /*
+ * nuri_set_edge_weights -- weights of the graph's edges, for isomorphism ranked by cumulative
+ * edge weight (NURI_RANK_EDGE_WEIGHT_SUM; Section 2, top-k semantics).
+ *   m, src, dst, w  m pairs (src[e], dst[e]) with weight w[e] >= 0, either direction.  An edge
+ *          given by several pairs weighs the largest of their weights; an edge given by none
+ *          weighs 0; self-loops are ignored.  Host arrays, or device arrays with
+ *          NURI_LOAD_DEVICE_INPUT in flags.  Nothing is kept of them after the call.
+ *   The call replaces the weights of an earlier call.  The graph must have labels (and its
+ *   label segments: not loaded with NURI_LOAD_NO_ISO).  Device memory: 12 bytes per directed
+ *   edge entry, plus 4 bytes per (vertex, label) and per label pair.
+ * Errors: NURI_ERR_INVALID (a pair that is not an edge of the graph, an id outside [0, n), a
+ * negative weight, an unlabelled graph; the graph keeps its previous weights), NURI_ERR_OOM,
+ * NURI_ERR_CUDA.
+ */
+nuri_status nuri_set_edge_weights(nuri_graph* g, int64_t m, const int32_t* src,
+                                  const int32_t* dst, const int32_t* w, uint32_t flags,
+                                  void* stream);
+
+/*
  * nuri_topk_cliques -- top-k cliques by size (Algorithm 1 with the clique functions of
  * Section 3.2: candidate set P_s of Listing 1 restricted by canonical extension, bound
  * |V_s| + |P_s| (Carraghan-Pardalos), prune a subgraph iff its bound < the k-th best size).
  *   k      >= 1
- *   rank   NURI_RANK_SIZE
+ *   rank   NURI_RANK_SIZE, or NURI_RANK_WEIGHT_SUM: cliques ranked by the sum of their vertex
+ *          weights (graph loaded with weights), bound w(V_s) + w(P_s), ties by sorted ids
+ *          (Section 2 leaves the ranking criterion to the user; frontier_cap is not used)
  *   flags  NURI_CLIQUE_ALL (default: every clique, singletons included, is a result) or
  *          NURI_CLIQUE_MAXIMAL; optionally NURI_KEEP_TIES, NURI_NO_PRUNE
  *   frontier_cap  maximum number of frontier records kept on the device before the lowest
@@ -179,9 +203,14 @@ nuri_status nuri_topk_cliques(nuri_graph* g, int32_t k, int32_t rank, uint32_t f
  * nuri_topk_iso -- top-k subgraphs isomorphic to a query (Section 2 definition, non-induced
  * image subgraphs; Section 4.3 functions: score = sum of vertex scores, upper bound =
  * score + sum over unmatched query vertices of index(root image, label, hop)).
- *   rank   NURI_RANK_WEIGHT_SUM or NURI_RANK_DEGREE_SUM
+ *   rank   NURI_RANK_WEIGHT_SUM or NURI_RANK_DEGREE_SUM, or NURI_RANK_EDGE_WEIGHT_SUM (score =
+ *          sum of the weights of the image's edges, nuri_set_edge_weights; upper bound =
+ *          score + for each unmatched query edge the largest weight an edge between its
+ *          endpoints' images could have: from a matched image, its heaviest edge to the
+ *          label; otherwise the heaviest edge between the two labels)
  *   flags  NURI_KEEP_TIES, NURI_ISO_INDUCED (induced matches only)
- * Errors: NURI_ERR_INVALID (nq outside 1..8, disconnected query, no labels/weights).
+ * Errors: NURI_ERR_INVALID (nq outside 1..8, disconnected query, no labels/weights/edge
+ * weights for the rank asked).
  */
 nuri_status nuri_topk_iso(nuri_graph* g, const nuri_query* q, int32_t k, int32_t rank,
                           uint32_t flags, void* stream, nuri_result** out);

@@ -22,7 +22,7 @@ __all__ = [
     "NuriError", "lib", "load_graph", "Graph", "topk_cliques", "topk_iso", "topk_iso_batch",
     "topk_patterns", "hop_index", "hop_index_noalloc", "set_time_budget", "tune_cliques", "Server",
     "request_bytes", "topk_batch", "Result", "LIB_PATH", "EXPORTS",
-    "RANK_SIZE", "RANK_WEIGHT_SUM", "RANK_DEGREE_SUM", "RANK_MNI",
+    "RANK_SIZE", "RANK_WEIGHT_SUM", "RANK_DEGREE_SUM", "RANK_MNI", "RANK_EDGE_WEIGHT_SUM",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -30,7 +30,7 @@ LIB_PATH = os.path.join(HERE, "libnuri.so")
 
 OK, ERR_INVALID, ERR_OOM, ERR_LIMIT, ERR_TIMEOUT, ERR_CANCELLED, ERR_CUDA, PENDING = range(8)
 REQ_CLIQUES, REQ_ISO, REQ_PATTERNS = 0, 1, 2
-RANK_SIZE, RANK_WEIGHT_SUM, RANK_DEGREE_SUM, RANK_MNI = range(4)
+RANK_SIZE, RANK_WEIGHT_SUM, RANK_DEGREE_SUM, RANK_MNI, RANK_EDGE_WEIGHT_SUM = range(5)
 LOAD_DEVICE_INPUT, LOAD_NO_ISO = 0x1, 0x2
 CLIQUE_ALL, CLIQUE_MAXIMAL = 0x0, 0x1
 KEEP_TIES, NO_PRUNE, ISO_INDUCED = 0x100, 0x200, 0x400
@@ -45,6 +45,7 @@ EXPORTS = (
     "nuri_server_create", "nuri_server_submit", "nuri_server_poll", "nuri_server_wait",
     "nuri_server_stats", "nuri_server_budget", "nuri_server_destroy", "nuri_request_bytes",
     "nuri_topk_batch", "nuri_server_clique_stats", "nuri_set_partition", "nuri_seed_part",
+    "nuri_set_edge_weights",
 )
 
 
@@ -135,6 +136,8 @@ def lib():
             L.nuri_free_graph.restype = None
             L.nuri_graph_get_info.argtypes = [P, ctypes.POINTER(_Info)]
             L.nuri_graph_get_info.restype = i32
+            L.nuri_set_edge_weights.argtypes = [P, i64, P, P, P, u32, P]
+            L.nuri_set_edge_weights.restype = i32
             L.nuri_topk_cliques.argtypes = [P, i32, i32, u32, i64, P, RPP]
             L.nuri_topk_cliques.restype = i32
             L.nuri_topk_iso.argtypes = [P, ctypes.POINTER(_Query), i32, i32, u32, P, RPP]
@@ -267,6 +270,25 @@ class Graph:
         _check(lib().nuri_graph_get_info(self.handle, ctypes.byref(inf)))
         return {f: getattr(inf, f) for f, _ in _Info._fields_ if f != "pad"}
 
+    def set_edge_weights(self, src, dst, w, stream=None):
+        """One weight (>= 0) per pair (src[e], dst[e]); an edge weighs the largest weight of
+        its pairs, 0 without any (host arrays or CUDA tensors)."""
+        keep = []
+        flags = 0
+        if hasattr(src, "is_cuda") and src.is_cuda:
+            flags |= LOAD_DEVICE_INPUT
+            ts = [t.contiguous() for t in (src, dst, w)]
+            keep += ts
+            ps, pd, pw = (ctypes.c_void_p(t.data_ptr()) for t in ts)
+            m = int(src.numel())
+        else:
+            s, ps = _host_ptr(src, np.int32)
+            d, pd = _host_ptr(dst, np.int32)
+            x, pw = _host_ptr(w, np.int32)
+            keep += [s, d, x]
+            m = int(s.size)
+        _check(lib().nuri_set_edge_weights(self.handle, m, ps, pd, pw, flags, _stream(stream)))
+
     def free(self):
         if self._h:
             lib().nuri_free_graph(self._h)
@@ -309,11 +331,13 @@ def load_graph(n, src, dst, labels=None, weights=None, index_hops=0, flags=0,
 
 
 def topk_cliques(g: Graph, k: int, maximal=False, keep_ties=False, no_prune=False,
-                 frontier_cap=0, stream=None) -> Result:
+                 frontier_cap=0, stream=None, weighted=False) -> Result:
+    """weighted: rank by the sum of the vertex weights (graph loaded with weights)."""
     flags = (CLIQUE_MAXIMAL if maximal else CLIQUE_ALL) | (KEEP_TIES if keep_ties else 0) | \
         (NO_PRUNE if no_prune else 0)
     rp = ctypes.POINTER(_Result)()
-    _check(lib().nuri_topk_cliques(g.handle, int(k), RANK_SIZE, flags, int(frontier_cap),
+    rank = RANK_WEIGHT_SUM if weighted else RANK_SIZE
+    _check(lib().nuri_topk_cliques(g.handle, int(k), rank, flags, int(frontier_cap),
                                    _stream(stream), ctypes.byref(rp)))
     return _unpack(rp)
 
@@ -326,19 +350,26 @@ def _query_struct(q, keep):
     return _Query(int(q.nq), int(s.size), lab.ctypes.data, s.ctypes.data, d.ctypes.data)
 
 
+def _iso_rank(degree_rank, edge_rank):
+    if edge_rank:
+        return RANK_EDGE_WEIGHT_SUM
+    return RANK_DEGREE_SUM if degree_rank else RANK_WEIGHT_SUM
+
+
 def topk_iso(g: Graph, q, k: int, degree_rank=False, keep_ties=False, stream=None,
-             induced=False) -> Result:
-    return topk_iso_batch(g, [q], [k], degree_rank, keep_ties, stream, induced)[0]
+             induced=False, edge_rank=False) -> Result:
+    """edge_rank: rank by the sum of the image's edge weights (Graph.set_edge_weights)."""
+    return topk_iso_batch(g, [q], [k], degree_rank, keep_ties, stream, induced, edge_rank)[0]
 
 
 def topk_iso_batch(g: Graph, queries, ks, degree_rank=False, keep_ties=False,
-                   stream=None, induced=False) -> list:
+                   stream=None, induced=False, edge_rank=False) -> list:
     keep = []
     nq = len(queries)
     arr = (_Query * nq)(*[_query_struct(q, keep) for q in queries])
     kk = np.ascontiguousarray(ks, dtype=np.int32)
     outs = (ctypes.POINTER(_Result) * nq)()
-    rank = RANK_DEGREE_SUM if degree_rank else RANK_WEIGHT_SUM
+    rank = _iso_rank(degree_rank, edge_rank)
     flags = (KEEP_TIES if keep_ties else 0) | (ISO_INDUCED if induced else 0)
     _check(lib().nuri_topk_iso_batch(g.handle, nq, arr, kk.ctypes.data_as(ctypes.c_void_p),
                                      rank, flags, _stream(stream), outs))
@@ -346,18 +377,22 @@ def topk_iso_batch(g: Graph, queries, ks, degree_rank=False, keep_ties=False,
 
 
 def _request(req, keep):
-    """A request tuple as the C struct: ("clique", k[, maximal[, keep_ties]]),
-    ("iso", query, k[, degree_rank[, keep_ties]]) or ("patterns", M, k[, keep_ties])."""
+    """A request tuple as the C struct: ("clique", k[, maximal[, keep_ties[, weighted]]]),
+    ("iso", query, k[, rank[, keep_ties]]) or ("patterns", M, k[, keep_ties]); an iso rank is
+    False (vertex weights), True (degrees) or "edge" (edge weights)."""
     kind = req[0]
     if kind == "clique":
         k = req[1]
         flags = (CLIQUE_MAXIMAL if len(req) > 2 and req[2] else 0) | \
             (KEEP_TIES if len(req) > 3 and req[3] else 0)
-        return _Request(REQ_CLIQUES, int(k), RANK_SIZE, flags, _Query(0, 0, None, None, None),
+        rank = RANK_WEIGHT_SUM if len(req) > 4 and req[4] else RANK_SIZE
+        return _Request(REQ_CLIQUES, int(k), rank, flags, _Query(0, 0, None, None, None),
                         0, 0)
     if kind == "iso":
         q, k = req[1], req[2]
-        rank = RANK_DEGREE_SUM if len(req) > 3 and req[3] else RANK_WEIGHT_SUM
+        r = req[3] if len(req) > 3 else False
+        edge = isinstance(r, str) and r == "edge"
+        rank = _iso_rank(bool(r) and not edge, edge)
         flags = KEEP_TIES if len(req) > 4 and req[4] else 0
         return _Request(REQ_ISO, int(k), rank, flags, _query_struct(q, keep), 0, 0)
     if kind == "patterns":

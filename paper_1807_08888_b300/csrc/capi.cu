@@ -27,6 +27,7 @@ void set_error(const char* fmt, ...) {
 const char* last_error() { return g_err; }
 
 static std::atomic<uint64_t> g_budget_ns{0};
+std::atomic<int> g_cuda_site{0};
 uint64_t time_budget_ns() { return g_budget_ns.load(); }
 
 __global__ void k_set_deadline(uint64_t* deadline, uint64_t budget_ns) {
@@ -136,6 +137,19 @@ void nuri_free_graph(nuri_graph* g) {
   cudaStreamSynchronize(s);
 }
 
+nuri_status nuri_set_edge_weights(nuri_graph* g, int64_t m, const int32_t* src,
+                                  const int32_t* dst, const int32_t* w, uint32_t flags,
+                                  void* stream) {
+  return guarded([&] {
+    if (!g) NURI_FAIL(NURI_ERR_INVALID, "nuri_set_edge_weights: NULL graph");
+    if (m < 0) NURI_FAIL(NURI_ERR_INVALID, "nuri_set_edge_weights: negative size");
+    if (m > 0 && (!src || !dst || !w))
+      NURI_FAIL(NURI_ERR_INVALID, "nuri_set_edge_weights: NULL arrays");
+    set_edge_weights(g, m, src, dst, w, (flags & NURI_LOAD_DEVICE_INPUT) != 0,
+                     (cudaStream_t)stream);
+  });
+}
+
 nuri_status nuri_graph_get_info(const nuri_graph* g, nuri_graph_info* info) {
   return guarded([&] {
     if (!g || !info) NURI_FAIL(NURI_ERR_INVALID, "nuri_graph_get_info: NULL argument");
@@ -190,9 +204,15 @@ nuri_status nuri_topk_cliques(nuri_graph* g, int32_t k, int32_t rank, uint32_t f
     if (!g || !out) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_cliques: NULL argument");
     *out = nullptr;
     if (k < 1) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_cliques: k must be >= 1");
-    if (rank != NURI_RANK_SIZE) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_cliques: rank must be NURI_RANK_SIZE");
+    if (rank != NURI_RANK_SIZE && rank != NURI_RANK_WEIGHT_SUM)
+      NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_cliques: rank must be NURI_RANK_SIZE or WEIGHT_SUM");
     if (frontier_cap < 0) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_cliques: negative frontier_cap");
-    topk_cliques(g, k, flags, frontier_cap, (cudaStream_t)stream, out);
+    if (rank == NURI_RANK_WEIGHT_SUM) {
+      if (!g->d.weights) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_cliques: graph has no weights");
+      topk_wcliques(g, k, flags, (cudaStream_t)stream, out);
+    } else {
+      topk_cliques(g, k, flags, frontier_cap, (cudaStream_t)stream, out);
+    }
   });
 }
 
@@ -208,11 +228,15 @@ nuri_status nuri_topk_iso_batch(nuri_graph* g, int32_t nqueries, const nuri_quer
     if (!g || !qs || !ks || !outs) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_iso: NULL argument");
     if (nqueries < 1) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_iso: no queries");
     for (int i = 0; i < nqueries; ++i) outs[i] = nullptr;
-    if (rank != NURI_RANK_WEIGHT_SUM && rank != NURI_RANK_DEGREE_SUM)
-      NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_iso: rank must be WEIGHT_SUM or DEGREE_SUM");
+    if (rank != NURI_RANK_WEIGHT_SUM && rank != NURI_RANK_DEGREE_SUM &&
+        rank != NURI_RANK_EDGE_WEIGHT_SUM)
+      NURI_FAIL(NURI_ERR_INVALID,
+                "nuri_topk_iso: rank must be WEIGHT_SUM, DEGREE_SUM or EDGE_WEIGHT_SUM");
     if (!g->d.labels || !g->d.lsoff) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_iso: graph has no labels");
     if (rank == NURI_RANK_WEIGHT_SUM && !g->d.weights)
       NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_iso: graph has no weights");
+    if (rank == NURI_RANK_EDGE_WEIGHT_SUM && !g->d.ew)
+      NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_iso: graph has no edge weights");
     for (int i = 0; i < nqueries; ++i) {
       if (ks[i] < 1) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_iso: k must be >= 1");
       const nuri_query& q = qs[i];
@@ -320,14 +344,20 @@ nuri_status nuri_topk_batch(nuri_graph* g, int32_t nreq, const nuri_request* req
       const nuri_request& r = reqs[i];
       if (r.k < 1) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_batch: request %d has k < 1", i);
       if (r.kind == NURI_REQ_CLIQUES) {
-        if (r.rank != NURI_RANK_SIZE) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_batch: request %d: clique rank must be NURI_RANK_SIZE", i);
+        if (r.rank != NURI_RANK_SIZE && r.rank != NURI_RANK_WEIGHT_SUM)
+          NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_batch: request %d: clique rank must be SIZE or WEIGHT_SUM", i);
+        if (r.rank == NURI_RANK_WEIGHT_SUM && !g->d.weights)
+          NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_batch: graph has no weights");
       } else if (r.kind == NURI_REQ_ISO) {
-        if (r.rank != NURI_RANK_WEIGHT_SUM && r.rank != NURI_RANK_DEGREE_SUM)
+        if (r.rank != NURI_RANK_WEIGHT_SUM && r.rank != NURI_RANK_DEGREE_SUM &&
+            r.rank != NURI_RANK_EDGE_WEIGHT_SUM)
           NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_batch: request %d: bad isomorphism rank", i);
         if (!query_ok(r.query)) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_batch: request %d: bad query", i);
         if (!g->d.labels || !g->d.lsoff) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_batch: graph has no labels");
         if (r.rank == NURI_RANK_WEIGHT_SUM && !g->d.weights)
           NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_batch: graph has no weights");
+        if (r.rank == NURI_RANK_EDGE_WEIGHT_SUM && !g->d.ew)
+          NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_batch: graph has no edge weights");
       } else if (r.kind == NURI_REQ_PATTERNS) {
         if (r.rank != NURI_RANK_MNI) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_batch: request %d: pattern rank must be NURI_RANK_MNI", i);
         if (r.pattern_edges < 1 || r.pattern_edges > 5)
@@ -343,7 +373,8 @@ nuri_status nuri_topk_batch(nuri_graph* g, int32_t nreq, const nuri_request* req
     for (int i = 0; i < nreq; ++i) {
       const nuri_request& r = reqs[i];
       uint64_t key = r.flags;
-      if (r.kind == NURI_REQ_ISO) key |= (uint64_t)(uint32_t)r.rank << 32;
+      if (r.kind == NURI_REQ_ISO || r.kind == NURI_REQ_CLIQUES)
+        key |= (uint64_t)(uint32_t)r.rank << 32;
       if (r.kind == NURI_REQ_PATTERNS) key |= (uint64_t)(uint32_t)r.pattern_edges << 32;
       auto it = std::find_if(groups.begin(), groups.end(), [&](const auto& x) {
         return x.first.first == r.kind && x.first.second == key;
@@ -356,8 +387,12 @@ nuri_status nuri_topk_batch(nuri_graph* g, int32_t nreq, const nuri_request* req
         const std::vector<int>& idx = grp.second;
         const nuri_request& r0 = reqs[idx[0]];
         if (r0.kind == NURI_REQ_CLIQUES) {
+          // the ranking is a total order that does not depend on k (by size or by weight,
+          // ties by sorted ids): every request is a prefix of the largest one
+          const bool weighted = r0.rank == NURI_RANK_WEIGHT_SUM;
           run_prefix_group(idx, reqs, r0.flags, [&](int32_t K, uint32_t fl, nuri_result** o) {
-            topk_cliques(g, K, fl, 0, s, o);
+            if (weighted) topk_wcliques(g, K, fl, s, o);
+            else topk_cliques(g, K, fl, 0, s, o);
           }, outs);
         } else if (r0.kind == NURI_REQ_PATTERNS) {
           run_prefix_group(idx, reqs, r0.flags, [&](int32_t K, uint32_t fl, nuri_result** o) {

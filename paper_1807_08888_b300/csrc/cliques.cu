@@ -39,10 +39,14 @@
 #include <cub/cub.cuh>
 
 #include <algorithm>
+#include <chrono>
 #include <climits>
+#include <condition_variable>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
+#include <thread>
 #include <vector>
 
 #include "nuri_internal.cuh"
@@ -66,7 +70,8 @@ struct Rec {
 
 struct QState {
   int32_t tau;
-  int32_t err;           // bit 0: clique larger than MAXD; bit 2: time budget exhausted
+  int32_t err;           // bit 0: clique larger than MAXD; bit 2: time budget exhausted;
+                         // bit 3: a corrupt frontier record (skipped, reported)
   int64_t res_count;     // results appended (may exceed the capacity: then a re-run)
   int64_t stage_count;   // children slots reserved in the staging array
   int64_t defer_count;   // parents sent back because the staging array was full
@@ -78,7 +83,74 @@ struct QState {
   unsigned long long tail_words;  // adjacency-row words combined by the task kernel
   unsigned long long lex_pruned;  // nodes pruned by the lexicographic tie bound
   int32_t hmax;          // largest clique size recorded so far
+  int32_t bad_nv;        // err bit 3: a frontier record that is not a clique record ...
+  int64_t bad_item;      // ... and its position in the launch's input
   int32_t hist[MAXD + 2];
+};
+
+// A query that runs under a time budget gets a watchdog thread: if the query is still running
+// 20 s after its budget ran out (every kernel checks the deadline, so it should have ended),
+// the thread reports on stderr, every 30 s, the source line of the query's last CUDA call and
+// a snapshot of its device state (copied on a stream of its own), and never touches the query.
+class QueryWatchdog {
+ public:
+  QueryWatchdog(const QState* dev_state, const std::atomic<int64_t>* rounds) {
+    const uint64_t budget = time_budget_ns();
+    if (!budget) return;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    th_ = std::thread([this, dev_state, rounds, budget, dev] {
+      using namespace std::chrono;
+      const auto t0 = steady_clock::now();
+      auto wait = nanoseconds(budget) + seconds(20);
+      std::unique_lock<std::mutex> lk(mu_);
+      while (!cv_.wait_for(lk, wait, [this] { return done_; })) {
+        wait = seconds(30);
+        // the host side first: no CUDA call, so that it is reported even when the query's
+        // thread holds the driver
+        fprintf(stderr,
+                "[nuri] clique query still running %.0f s after its start: round %lld, last "
+                "CUDA call at cliques/capi line %d\n",
+                duration<double>(steady_clock::now() - t0).count(), (long long)rounds->load(),
+                g_cuda_site.load(std::memory_order_relaxed));
+        fflush(stderr);
+        QState h;
+        memset(&h, 0, sizeof(h));
+        cudaSetDevice(dev);
+        cudaStream_t ws = nullptr;
+        bool copied = false;
+        if (cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) == cudaSuccess) {
+          copied = cudaMemcpyAsync(&h, dev_state, sizeof(h), cudaMemcpyDeviceToHost, ws) ==
+                       cudaSuccess &&
+                   cudaStreamSynchronize(ws) == cudaSuccess;
+          cudaStreamDestroy(ws);
+        }
+        fprintf(stderr,
+                "[nuri]   device state%s: tau %d err %d results %lld work_next %lld staged "
+                "%lld deferred %lld dense %lld/%lld/%lld nodes %llu\n",
+                copied ? "" : " (not read)", h.tau, h.err, (long long)h.res_count,
+                (long long)h.work_next,
+                (long long)h.stage_count, (long long)h.defer_count, (long long)h.small_count,
+                (long long)h.mid_count, (long long)h.wide_count, h.expansions);
+        fflush(stderr);
+      }
+    });
+  }
+  ~QueryWatchdog() {
+    if (!th_.joinable()) return;
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      done_ = true;
+    }
+    cv_.notify_all();
+    th_.join();
+  }
+
+ private:
+  std::mutex mu_;
+  std::condition_variable cv_;
+  bool done_ = false;
+  std::thread th_;
 };
 
 __device__ __forceinline__ int lower_bound_dev(const int32_t* a, int lo, int hi, int32_t x) {
@@ -387,7 +459,9 @@ __device__ __forceinline__ void and_live(unsigned long long* out, const unsigned
 // continuation tasks (nodes already visited, with the candidates not yet branched on), so the
 // next wave spreads that subtree over the GPU instead of leaving it to one lane.
 // ---------------------------------------------------------------------------------------------
-constexpr int kSliceNodes = 1 << 14;  // nodes a lane searches before it hands its stack on
+constexpr int kSliceNodes = 1 << 14;  // nodes a lane searches before it sheds work
+constexpr int kShed = 8;              // levels shed at a time
+constexpr int kFullHandOff = 64;      // pending levels a lane hands on in one go
 // Device memory bounds of one query's buffers (they make the server's admission estimate an
 // upper bound): records handed to the dense tiers or sent back per round, and the dense store
 constexpr int64_t kRoundRecs = 1 << 16;
@@ -646,18 +720,55 @@ __device__ void dense_node(const Ctx& cx, const WideStore& ws, int slot, int dep
     if (fresh) {
       fresh = false;
       const int size = nv + depth + 1;
-      // hand the rest of the stack on once the wave's input is used up, or once this lane
-      // has searched kSliceNodes nodes (so that no wave runs long between the host's
-      // threshold and tie-bound updates), when there is room: the current node and every
-      // level below it that still has vertices to branch on
-      if (split && ++local >= 16 && (local & 15) == 0 &&
-          ((int64_t)ld_volatile(ws.in_next) >= ws.in_n || local >= kSliceNodes) &&
+      // past kSliceNodes nodes while the wave still has input, every 1024 nodes: shed the
+      // untried branches of the (at most kShed) shallowest levels below the current node as
+      // tasks and keep searching the current path, so that deep searches spread over the
+      // next waves (between which the host refreshes the threshold and the tie bound).  A
+      // shed level's remaining cliques are those inside its untried candidates: the task
+      // (cont = 1, candidates = the untried set) enumerates them; the level here stops.
+      const bool drained = (int64_t)ld_volatile(ws.in_next) >= ws.in_n;
+      if (split && local >= (drained ? 1024 : kSliceNodes) && (local & 1023) == 0 &&
+          (int64_t)ld_volatile(ws.q_count) < ws.q_cap / 2) {
+        int r = 0;
+        for (int l = base_depth; l < depth && r < kShed; ++l) r += any<W>(stkR[l], wa) ? 1 : 0;
+        if (r > 0) {
+          const unsigned long long base = atomicAdd(ws.q_count, (unsigned long long)r);
+          if ((int64_t)(base + r) <= ws.q_cap) {
+            int k = 0;
+            for (int l = base_depth; l < depth && k < r; ++l) {
+              if (!any<W>(stkR[l], wa)) continue;
+              WTask* t = ws.q_out + base + (k++);
+              t->slot = slot;
+              t->depth = (int16_t)l;
+              t->cont = 1;
+              write_picks(t, pick, l);
+#pragma unroll
+              for (int q = 0; q < KWIDE; ++q) {
+                t->P[q] = q < wa ? stkP[l][q] : 0ull;
+                if (cx.maximal) t->X[q] = q < wa ? stkX[l][q] : 0ull;
+              }
+#pragma unroll
+              for (int q = 0; q < W; ++q)
+                if (q < wa) stkR[l][q] = 0ull;
+            }
+          } else {
+            for (unsigned long long q = base; q < base + r && (int64_t)q < ws.q_cap; ++q)
+              ws.q_out[q].slot = -1;
+          }
+        }
+      }
+      // hand the rest of the stack on once the wave's input is used up (and there is room):
+      // the current node and every level below it that still has vertices to branch on.  A
+      // stack with more than kFullHandOff such levels, or a hand-off that found no room, is
+      // shed a few levels at a time instead (above).
+      if (split && ++local >= 16 && (local & 15) == 0 && drained &&
           (int64_t)ld_volatile(ws.q_count) < ws.q_cap / 2) {
         int r = any<W>(Pn, wa) ? 1 : 0;
         for (int l = base_depth; l < depth; ++l) r += any<W>(stkR[l], wa) ? 1 : 0;
         if (r == 0) break;
-        const unsigned long long base = atomicAdd(ws.q_count, (unsigned long long)r);
-        if ((int64_t)(base + r) <= ws.q_cap) {
+        const unsigned long long base =
+            r <= kFullHandOff ? atomicAdd(ws.q_count, (unsigned long long)r) : ~0ull;
+        if (r <= kFullHandOff && (int64_t)(base + r) <= ws.q_cap) {
           int k = 0;
           for (int l = base_depth; l <= depth; ++l) {
             if (l < depth ? !any<W>(stkR[l], wa) : !any<W>(Pn, wa)) continue;
@@ -676,9 +787,9 @@ __device__ void dense_node(const Ctx& cx, const WideStore& ws, int slot, int dep
           }
           return;
         }
-        for (unsigned long long q = base; q < base + r && (int64_t)q < ws.q_cap; ++q)
-          ws.q_out[q].slot = -1;
-        local = INT32_MIN;  // no room: finish here
+        if (r <= kFullHandOff)
+          for (unsigned long long q = base; q < base + r && (int64_t)q < ws.q_cap; ++q)
+            ws.q_out[q].slot = -1;
       }
       unsigned long long R[W];
 #pragma unroll
@@ -882,9 +993,33 @@ __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
       if (lane == 0) sV[w][0] = seeds[item];
     } else {
       nv = in[item].nv;
+      if (nv < 1 || nv > MAXD) {  // not a record: reported, never followed
+        if (lane == 0) {
+          cx.st->bad_nv = nv;
+          cx.st->bad_item = item;
+          atomicOr(&cx.st->err, 8);
+        }
+        continue;
+      }
       for (int i = lane; i < nv; i += 32) sV[w][i] = in[item].V[i];
     }
     __syncwarp();
+    {
+      // members: ranks of the graph in increasing order
+      bool ok = true;
+      for (int i = lane; i < nv; i += 32) {
+        const int32_t v = sV[w][i];
+        ok = ok && v >= 0 && v < g.n && (i == 0 || sV[w][i - 1] < v);
+      }
+      if (!__all_sync(FULL, ok)) {
+        if (lane == 0) {
+          cx.st->bad_nv = nv;
+          cx.st->bad_item = item;
+          atomicOr(&cx.st->err, 8);
+        }
+        continue;
+      }
+    }
     if (lane == 0) ++my_deq;
 
     // ---- candidate set P (ranks after every member, adjacent to all members) ----
@@ -914,6 +1049,13 @@ __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
         int32_t* dst = (ce - cb) <= PSMEM ? sP[w] : scratch;
         int cnt = 0;
         for (int64_t base = cb; base < ce; base += 32) {
+          if (((base - cb) & 4095) == 4064) {  // a long row: stop at the deadline (uniform)
+            int late = lane == 0 && past_deadline(cx);
+            if (__shfl_sync(FULL, late, 0)) {
+              if (lane == 0) atomicOr(&cx.st->err, 4);
+              break;
+            }
+          }
           int64_t t = base + lane;
           bool keep = false;
           int32_t x = 0;
@@ -938,7 +1080,7 @@ __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
     }
 
     // ---- dequeue: prune (dominated), then result insertion ----
-    int32_t tau = ld_volatile(&cx.st->tau);
+    const int32_t tau = warp_load(&cx.st->tau);  // one value for the warp's branches
     int bound = nv + p;
     if (!cx.no_prune && bound < tau) {
       if (lane == 0) ++my_pruned;
@@ -1071,7 +1213,7 @@ __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
       // candidates a clique reaching tau needs below this record (0: no core filter)
       int core_need = 0;
       if (!cx.no_prune) {
-        const int32_t t_now = ld_volatile(&cx.st->tau);
+        const int32_t t_now = warp_load(&cx.st->tau);  // core_need steers warp-wide code
         if (t_now != INT32_MIN && t_now - nv > 1) core_need = t_now - nv;
       }
       // candidates inside the core bitmap (the last ranks of the order): rows come from bit
@@ -1568,6 +1710,13 @@ __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
     // ================= split: one child per d in P, pushed to the staging array =================
     const int32_t plast = P[p - 1];
     for (int j = 0; j < p; ++j) {
+      if ((j & 63) == 63) {  // a long record: stop at the deadline (uniform)
+        int late = lane == 0 && past_deadline(cx);
+        if (__shfl_sync(FULL, late, 0)) {
+          if (lane == 0) atomicOr(&cx.st->err, 4);
+          break;
+        }
+      }
       int32_t d = P[j];
       int64_t rb = g.ooff[d], re = g.ooff[d + 1];
       int64_t re2 = lower_bound_dev64(g.oout, rb, re, plast + 1);
@@ -2591,6 +2740,8 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
 
   DBuf<QState> st;
   st.alloc(1, s);
+  std::atomic<int64_t> rounds_seen{0};  // read by the watchdog
+  QueryWatchdog watchdog(st.p, &rounds_seen);
   DBuf<uint64_t> deadline;
   deadline.alloc(1, s);
   ++launches;
@@ -2765,6 +2916,11 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
     while (true) {
       NURI_CUDA(cudaMemcpyAsync(&hs, st.p, sizeof(hs), cudaMemcpyDeviceToHost, s));
       NURI_CUDA(cudaStreamSynchronize(s));
+      if (hs.err & 8)
+        NURI_FAIL(NURI_ERR_CUDA,
+                  "nuri_topk_cliques: internal error: frontier record %lld of round %lld is not "
+                  "a clique record (nv %d)",
+                  (long long)hs.bad_item, (long long)rounds, hs.bad_nv);
       if (hs.err & 1) NURI_FAIL(NURI_ERR_LIMIT, "nuri_topk_cliques: a clique exceeds %d vertices", MAXD);
       if (hs.err & 4)
         NURI_FAIL(NURI_ERR_TIMEOUT,
@@ -2878,6 +3034,7 @@ void topk_cliques(nuri_graph* G, int32_t k, uint32_t flags, int64_t frontier_cap
       }
       NURI_CUDA(cudaGetLastError());
       ++rounds;
+      rounds_seen.fetch_add(1, std::memory_order_relaxed);
       if (trace) {
         float ms = 0.f;
         NURI_CUDA(cudaStreamSynchronize(s));

@@ -136,90 +136,168 @@ __global__ void k_peel_remove(const int64_t* __restrict__ off, const int32_t* __
   }
 }
 
-// The unassigned vertices (batch < 0), compacted into list (order not kept).
-__global__ void k_peel_list(const int32_t* __restrict__ batch, int32_t n,
-                            int32_t* __restrict__ list, int32_t* cnt) {
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
-       v += (int64_t)gridDim.x * blockDim.x)
-    if (batch[v] < 0) list[atomicAdd(cnt, 1)] = (int32_t)v;
-}
-
-// The rest of the peel in one CTA, once few vertices remain (the long tail of small batches
-// would otherwise cost a launch and a host round trip each).  Same rule as the batch loop on
-// the host: when the front is empty, k rises to the smallest remaining degree and every
-// unassigned vertex with remaining degree <= k forms batch b; removing a batch lowers its
-// neighbours' degrees and those that drop to <= k form batch b + 1.  list/nlist: the
-// unassigned vertices (la, lb: two buffers of that size); fa, fb: fronts (same size);
-// front/nfront: the current front (batch b), k, b: the current level and batch.
-// out[0] = the largest k reached, out[1] = 0 on success, 1 if a front came out empty while
-// vertices remained (cannot happen; reported instead of looping).
+// The rest of the peel in one CTA, once at most kTailVertices vertices are left (the long
+// tail of small batches would otherwise cost a launch and a host round trip each).  Same rule
+// as the batch loop on the host: when the front is empty, k rises to the smallest remaining
+// degree and every unassigned vertex with remaining degree <= k forms batch b; removing a
+// batch lowers its neighbours' degrees and those that drop to <= k form batch b + 1.
+//
+// The tail runs on a local copy of the subgraph it still touches, so that every step of a
+// batch is a shared-memory atomic instead of a chain of global ones:
+//   local ids [0, nf) are the current front (assigned, not yet removed), [nf, nl) the
+//   unassigned vertices; gid maps a local id to its vertex, loc the other way (-1 outside);
+//   the local row of i (loff/ladj, 16-bit local ids) lists i's unassigned neighbours.
+// Shared memory holds each local vertex's remaining degree as a 16-bit half of a 32-bit word
+// (a degree never passes nl - 1 <= 65535 in a simple graph, and never goes below zero, so
+// the halves never borrow from each other) and one assigned bit per local vertex.
+constexpr int32_t kTailVertices = 1 << 16;
 constexpr int64_t kHeavyRow = 512;  // rows longer than this are walked by the whole CTA
 constexpr int kHeavyList = 256;     // heavy rows per batch handled that way (the rest by warps)
+
+__global__ void k_tail_ids(const int32_t* __restrict__ batch, int32_t n,
+                           const int32_t* __restrict__ front, int32_t nf, int32_t nl,
+                           int32_t* __restrict__ gid, int32_t* __restrict__ loc, int32_t* cnt) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    if (v < nf) {
+      gid[v] = front[v];
+      loc[front[v]] = (int32_t)v;
+    }
+    if (batch[v] < 0) {
+      const int32_t i = nf + atomicAdd(cnt, 1);
+      if (i < nl) {  // the host checks the count before using the ids
+        gid[i] = (int32_t)v;
+        loc[v] = i;
+      }
+    }
+  }
+}
+
+// one warp per local vertex: the number of its unassigned neighbours
+__global__ void k_tail_count(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+                             const int32_t* __restrict__ gid, const int32_t* __restrict__ loc,
+                             int32_t nl, int32_t nf, int64_t* __restrict__ lcnt) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < nl;
+       i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int32_t v = gid[i];
+    int32_t c = 0;
+    for (int64_t t = off[v] + lane; t < off[v + 1]; t += 32) c += loc[adj[t]] >= nf;
+    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) lcnt[i] = c;
+  }
+}
+
+__global__ void k_tail_fill(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+                            const int32_t* __restrict__ gid, const int32_t* __restrict__ loc,
+                            int32_t nl, int32_t nf, const int64_t* __restrict__ loff,
+                            uint16_t* __restrict__ ladj) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < nl;
+       i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int32_t v = gid[i];
+    int64_t pos = loff[i];
+    for (int64_t t0 = off[v]; t0 < off[v + 1]; t0 += 32) {
+      const int64_t t = t0 + lane;
+      const int32_t u = t < off[v + 1] ? loc[adj[t]] : -1;
+      const bool keep = u >= nf;
+      const unsigned m = __ballot_sync(0xffffffffu, keep);
+      if (keep) ladj[pos + __popc(m & ((1u << lane) - 1))] = (uint16_t)u;
+      pos += __popc(m);
+    }
+  }
+}
+
+// out[0] = the largest k reached; out[1] = 0 on success, 1 if a front came out empty while
+// vertices remained, 2 if a remaining degree did not fit 16 bits (neither can happen; both
+// reported instead of looping or miscounting).
 __global__ void __launch_bounds__(1024) k_peel_tail(
-    const int64_t* __restrict__ off, const int32_t* __restrict__ adj, int32_t* __restrict__ rem,
-    int32_t* __restrict__ batch, int32_t* la, int32_t* lb, int32_t nlist, int32_t* fa,
-    int32_t* fb, int32_t nfront0, int32_t k0, int32_t b0, int32_t* out) {
-  __shared__ int32_t s_nlist, s_nfront, s_nnext, s_k, s_min, s_cnt, s_nheavy;
+    const int64_t* __restrict__ loff, const uint16_t* __restrict__ ladj,
+    const int32_t* __restrict__ gid, const int32_t* __restrict__ rem, int32_t nl, int32_t nf0,
+    int32_t k0, int32_t b0, int32_t* __restrict__ batch, int32_t* fa, int32_t* fb,
+    int32_t* out) {
+  extern __shared__ uint32_t s_dyn[];
+  uint32_t* s_rem = s_dyn;                    // (nl + 1) / 2 words, two 16-bit degrees each
+  uint32_t* s_done = s_dyn + (nl + 1) / 2;    // (nl + 31) / 32 words, one assigned bit each
+  __shared__ int32_t s_nfront, s_nnext, s_k, s_min, s_nheavy, s_bad;
   __shared__ int32_t s_heavy[kHeavyList];
-  __shared__ int64_t s_remaining;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
-  int32_t* list = la;
-  int32_t* list2 = lb;
+  const int32_t nwords = (nl + 31) / 32;
+  if (tid == 0) s_bad = 0;
+  __syncthreads();
+  for (int32_t w = tid; w < (nl + 1) / 2; w += nthr) {
+    uint32_t lo = 0, hi = 0;
+    const int32_t i = 2 * w;
+    if (i >= nf0) lo = (uint32_t)rem[gid[i]];
+    if (i + 1 < nl && i + 1 >= nf0) hi = (uint32_t)rem[gid[i + 1]];
+    if ((lo | hi) > 0xffffu) atomicExch(&s_bad, 1);
+    s_rem[w] = (lo & 0xffffu) | (hi << 16);
+  }
+  for (int32_t w = tid; w < nwords; w += nthr) {
+    uint32_t bits = 0;  // the front is assigned; bits past nl stay set so scans skip them
+    for (int j = 0; j < 32; ++j) {
+      const int32_t i = w * 32 + j;
+      if (i < nf0 || i >= nl) bits |= 1u << j;
+    }
+    s_done[w] = bits;
+  }
+  for (int32_t i = tid; i < nf0; i += nthr) fa[i] = i;
+  if (tid == 0) {
+    s_nfront = nf0;
+    s_nnext = 0;
+    s_k = k0;
+    s_nheavy = 0;
+  }
+  __syncthreads();
+  if (s_bad) {
+    if (tid == 0) out[1] = 2;
+    return;
+  }
   int32_t* front = fa;
   int32_t* next = fb;
   int32_t b = b0;
-  if (tid == 0) {
-    s_nheavy = 0;
-    s_nlist = nlist;
-    s_nfront = nfront0;
-    s_nnext = 0;
-    s_k = k0;
-    s_remaining = nlist;  // the current front is still in the list (batch >= 0 there)
-  }
-  __syncthreads();
-  // the list holds the front too: count the unassigned part
-  if (tid == 0) s_cnt = 0;
-  __syncthreads();
-  for (int i = tid; i < s_nlist; i += nthr)
-    if (batch[list[i]] < 0) atomicAdd(&s_cnt, 1);
-  __syncthreads();
-  if (tid == 0) s_remaining = (int64_t)s_cnt + s_nfront;
-  __syncthreads();
-  while (s_remaining > 0) {
+  int32_t remaining = nl;
+  auto rem_of = [&](int32_t i) -> int32_t { return (s_rem[i >> 1] >> ((i & 1) * 16)) & 0xffffu; };
+  while (remaining > 0) {
     if (s_nfront == 0) {
-      // compact the list to the unassigned vertices, take their smallest remaining degree
-      if (tid == 0) {
-        s_cnt = 0;
-        s_min = INT32_MAX;
-      }
+      // k rises to the smallest remaining degree; every unassigned vertex at or below it
+      // forms batch b
+      if (tid == 0) s_min = INT32_MAX;
       __syncthreads();
-      const int32_t nl = s_nlist;
-      for (int i = tid; i < nl; i += nthr) {
-        const int32_t v = list[i];
-        if (batch[v] < 0) {
-          list2[atomicAdd(&s_cnt, 1)] = v;
-          atomicMin(&s_min, rem[v]);
+      int32_t mn = INT32_MAX;
+      for (int32_t w = tid; w < nwords; w += nthr) {
+        uint32_t open = ~s_done[w];
+        while (open) {
+          const int j = __ffs(open) - 1;
+          open &= open - 1;
+          mn = min(mn, rem_of(w * 32 + j));
         }
       }
+      for (int o = 16; o; o >>= 1) mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+      if (lane == 0) atomicMin(&s_min, mn);
       __syncthreads();
-      {
-        int32_t* t = list;
-        list = list2;
-        list2 = t;
-      }
-      if (tid == 0) {
-        s_nlist = s_cnt;
-        s_k = max(s_k, s_min);
-        s_nfront = 0;
-      }
+      if (tid == 0) s_k = max(s_k, s_min);
       __syncthreads();
       const int32_t k = s_k;
-      for (int i = tid; i < s_nlist; i += nthr) {
-        const int32_t v = list[i];
-        if (rem[v] <= k) {
-          batch[v] = b;
-          front[atomicAdd(&s_nfront, 1)] = v;
+      for (int32_t w = tid; w < nwords; w += nthr) {
+        uint32_t open = ~s_done[w], take = 0;
+        while (open) {
+          const int j = __ffs(open) - 1;
+          open &= open - 1;
+          if (rem_of(w * 32 + j) <= k) take |= 1u << j;
+        }
+        if (take) {
+          s_done[w] |= take;  // one thread owns each word here
+          const int c = __popc(take);
+          int32_t at = atomicAdd(&s_nfront, c);
+          while (take) {
+            const int j = __ffs(take) - 1;
+            take &= take - 1;
+            const int32_t i = w * 32 + j;
+            front[at++] = i;
+            batch[gid[i]] = b;
+          }
         }
       }
       __syncthreads();
@@ -232,13 +310,19 @@ __global__ void __launch_bounds__(1024) k_peel_tail(
     // light front vertices: one warp each; heavy ones (long rows): the whole CTA, one at a
     // time, so that a hub's row is not walked by one warp's chain of atomics
     auto drop = [&](int32_t u) {
-      if (*(volatile int32_t*)(batch + u) >= 0) return;
-      const int32_t old = atomicSub(rem + u, 1);
-      if (old - 1 <= k && atomicCAS(batch + u, -1, b + 1) == -1) next[atomicAdd(&s_nnext, 1)] = u;
+      const uint32_t bit = 1u << (u & 31);
+      if (s_done[u >> 5] & bit) return;
+      const int sh = (u & 1) * 16;
+      const int32_t old = (int32_t)((atomicSub(&s_rem[u >> 1], 1u << sh) >> sh) & 0xffffu);
+      if (old - 1 <= k && !(atomicOr(&s_done[u >> 5], bit) & bit)) {
+        next[atomicAdd(&s_nnext, 1)] = u;
+        batch[gid[u]] = b + 1;
+      }
     };
     for (int w = warp; w < nf; w += nwarps) {
       const int32_t v = front[w];
-      if (off[v + 1] - off[v] > kHeavyRow) {
+      const int64_t lo = loff[v], hi = loff[v + 1];
+      if (hi - lo > kHeavyRow) {
         int slot = -1;
         if (lane == 0) slot = atomicAdd(&s_nheavy, 1);
         slot = __shfl_sync(0xffffffffu, slot, 0);
@@ -247,27 +331,35 @@ __global__ void __launch_bounds__(1024) k_peel_tail(
           continue;
         }
       }
-      for (int64_t t = off[v] + lane; t < off[v + 1]; t += 32) drop(adj[t]);
+      // four loads in flight per lane before the atomics that use them
+      for (int64_t t = lo + lane; t < hi; t += 128) {
+        int32_t u[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) u[q] = t + 32 * q < hi ? (int32_t)ladj[t + 32 * q] : -1;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (u[q] >= 0) drop(u[q]);
+      }
     }
     __syncthreads();
     const int nh = min(s_nheavy, kHeavyList);
     for (int h = 0; h < nh; ++h) {
       const int32_t v = s_heavy[h];
-      for (int64_t t = off[v] + tid; t < off[v + 1]; t += nthr) drop(adj[t]);
+      for (int64_t t = loff[v] + tid; t < loff[v + 1]; t += nthr) drop(ladj[t]);
     }
     __syncthreads();
-    if (tid == 0) s_nheavy = 0;
     {
       int32_t* t = front;
       front = next;
       next = t;
     }
+    remaining -= nf;
+    ++b;
     if (tid == 0) {
-      s_remaining -= nf;
+      s_nheavy = 0;
       s_nfront = s_nnext;
       s_nnext = 0;
     }
-    ++b;
     __syncthreads();
   }
   if (tid == 0) {
@@ -607,7 +699,6 @@ void build_label_segments(const DevGraph& d, const uint64_t* ckeys, const int32_
 // kMaxPeelBatches batches (then the caller uses the degree order).
 static bool peel_order(nuri_graph* g, uint64_t* keys, cudaStream_t s) {
   constexpr int kMaxPeelBatches = 20000;
-  constexpr int64_t kTailVertices = 1 << 16;  // at most this many left: one-CTA tail kernel
   const int32_t n = g->d.n;
   DBuf<int32_t> rem, batch, fa, fb, cnt;
   rem.alloc(n, s);
@@ -624,19 +715,43 @@ static bool peel_order(nuri_graph* g, uint64_t* keys, cudaStream_t s) {
   while (remaining > 0) {
     if (b > kMaxPeelBatches) return false;
     if (remaining <= kTailVertices) {
-      // finish on the device in one CTA
-      DBuf<int32_t> la, lb, tout;
-      la.alloc(remaining, s);
-      lb.alloc(remaining, s);
+      // finish on the device in one CTA, on the local subgraph of what is left
+      const int32_t nl = (int32_t)remaining;
+      DBuf<int32_t> gid, loc, tout;
+      DBuf<int64_t> lcnt, loff;
+      gid.alloc(nl, s);
+      loc.alloc(n, s);
+      lcnt.alloc(nl + 1, s);
+      loff.alloc(nl + 1, s);
       tout.alloc(2, s);
+      NURI_CUDA(cudaMemsetAsync(loc.p, 0xff, sizeof(int32_t) * (size_t)n, s));
       NURI_CUDA(cudaMemsetAsync(cnt.p, 0, 4, s));
-      k_peel_list<<<blocks_for(n), kThreads, 0, s>>>(batch.p, n, la.p, cnt.p);
-      int32_t nl = 0;
-      NURI_CUDA(cudaMemcpyAsync(&nl, cnt.p, 4, cudaMemcpyDeviceToHost, s));
+      k_tail_ids<<<blocks_for(n), kThreads, 0, s>>>(batch.p, n, front, nfront, nl, gid.p, loc.p,
+                                                    cnt.p);
+      NURI_CUDA(cudaMemsetAsync(lcnt.p + nl, 0, sizeof(int64_t), s));
+      const int wgrid = (int)std::min<int64_t>((nl + 7) / 8, sm_count() * 16);
+      k_tail_count<<<wgrid, 256, 0, s>>>(g->off.p, g->adj.p, gid.p, loc.p, nl, nfront, lcnt.p);
+      size_t tb = 0;
+      cub::DeviceScan::ExclusiveSum(nullptr, tb, lcnt.p, loff.p, nl + 1, s);
+      DBuf<uint8_t> tmp;
+      tmp.alloc(tb, s);
+      NURI_CUDA(cub::DeviceScan::ExclusiveSum(tmp.p, tb, lcnt.p, loff.p, nl + 1, s));
+      int32_t nu = 0;
+      int64_t lnnz = 0;
+      NURI_CUDA(cudaMemcpyAsync(&nu, cnt.p, 4, cudaMemcpyDeviceToHost, s));
+      NURI_CUDA(cudaMemcpyAsync(&lnnz, loff.p + nl, 8, cudaMemcpyDeviceToHost, s));
       NURI_CUDA(cudaStreamSynchronize(s));
-      // fronts need room for every remaining vertex; fa/fb hold n entries
-      k_peel_tail<<<1, 1024, 0, s>>>(g->off.p, g->adj.p, rem.p, batch.p, la.p, lb.p, nl, front,
-                                     next, nfront, k, b, tout.p);
+      if ((int64_t)nu + nfront != nl) return false;  // the count kept on the host is off
+      DBuf<uint16_t> ladj;
+      ladj.alloc(std::max<int64_t>(lnnz, 1), s);
+      k_tail_fill<<<wgrid, 256, 0, s>>>(g->off.p, g->adj.p, gid.p, loc.p, nl, nfront, loff.p,
+                                        ladj.p);
+      const size_t smem = sizeof(uint32_t) * (size_t)((nl + 1) / 2 + (nl + 31) / 32);
+      NURI_CUDA(cudaFuncSetAttribute(k_peel_tail, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+      // fronts hold local ids; fa/fb have room for n >= nl entries
+      k_peel_tail<<<1, 1024, smem, s>>>(loff.p, ladj.p, gid.p, rem.p, nl, nfront, k, b,
+                                        batch.p, front, next, tout.p);
       NURI_CUDA(cudaGetLastError());
       int32_t to[2] = {0, 1};
       NURI_CUDA(cudaMemcpyAsync(to, tout.p, 8, cudaMemcpyDeviceToHost, s));
@@ -693,6 +808,178 @@ __global__ void k_core_bits(const int64_t* __restrict__ ooff, const int32_t* __r
       atomicOr(&bits[(int64_t)x * words + (w >> 6)], 1ull << (w & 63));
     }
   }
+}
+
+// ---- edge weights (ranking isomorphism matches by cumulative edge weight) -------------------
+namespace {
+
+// Position of b in the id-sorted row of a, or -1.
+__device__ __forceinline__ int64_t row_find(const int64_t* __restrict__ off,
+                                            const int32_t* __restrict__ adj, int32_t a,
+                                            int32_t b) {
+  int64_t lo = off[a], hi = off[a + 1];
+  const int64_t end = hi;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (__ldg(adj + mid) < b) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo < end && __ldg(adj + lo) == b ? lo : -1;
+}
+
+// Every pair (a, b), a != b, raises both directions of its edge to at least w; flag[0]: an id
+// outside [0, n), flag[1]: a negative weight, flag[2]: a pair that is not an edge.
+__global__ void k_ew_scatter(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+                             int32_t n, const int32_t* __restrict__ src,
+                             const int32_t* __restrict__ dst, const int32_t* __restrict__ w,
+                             int64_t m, int32_t* __restrict__ ew, int32_t* flag) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t a = src[e], b = dst[e], x = w[e];
+    if (a < 0 || a >= n || b < 0 || b >= n) {
+      atomicOr(flag + 0, 1);
+      continue;
+    }
+    if (x < 0) {
+      atomicOr(flag + 1, 1);
+      continue;
+    }
+    if (a == b) continue;  // self-loops are not edges of the graph
+    const int64_t pa = row_find(off, adj, a, b), pb = row_find(off, adj, b, a);
+    if (pa < 0 || pb < 0) {
+      atomicOr(flag + 2, 1);
+      continue;
+    }
+    atomicMax(ew + pa, x);
+    atomicMax(ew + pb, x);
+  }
+}
+
+// One warp per row v: emax[v*L + label(u)] over the row's entries, and the sort keys of the
+// edge-weight-ranked segments: (v*L + label(u)) << 32 | (INT32_MAX - w), value = entry index
+// (the radix sort is stable, so equal weights keep the id order of the row).
+__global__ void k_ew_rows(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+                          const uint8_t* __restrict__ labels, const int32_t* __restrict__ ew,
+                          int32_t n, int32_t L, int32_t* __restrict__ emax,
+                          uint64_t* __restrict__ keys, int64_t* __restrict__ vals) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t v = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; v < n;
+       v += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    for (int64_t t = off[v] + lane; t < off[v + 1]; t += 32) {
+      const int32_t u = adj[t], x = ew[t], l = labels[u];
+      atomicMax(emax + v * L + l, x);
+      keys[t] = ((uint64_t)(v * L + l) << 32) | (uint32_t)(INT32_MAX - x);
+      vals[t] = t;
+    }
+  }
+}
+
+// lpmax[label(v)*L + l] = max over v of emax[v*L + l] (a plain read first keeps most threads
+// off the atomic once the maxima are reached)
+__global__ void k_ew_labelpairs(const uint8_t* __restrict__ labels,
+                                const int32_t* __restrict__ emax, int32_t n, int32_t L,
+                                int32_t* lpmax) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)n * L;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t x = emax[i];
+    if (x < 0) continue;
+    int32_t* cell = lpmax + (int64_t)labels[i / L] * L + (i % L);
+    if (x > *(volatile int32_t*)cell) atomicMax(cell, x);
+  }
+}
+
+__global__ void k_ew_segments(const int64_t* __restrict__ order, int64_t nnz,
+                              const int32_t* __restrict__ adj, const int32_t* __restrict__ ew,
+                              int2* __restrict__ seg) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nnz;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = order[i];
+    seg[i] = make_int2(adj[t], ew[t]);
+  }
+}
+
+}  // namespace
+
+void set_edge_weights(nuri_graph* g, int64_t m, const int32_t* src, const int32_t* dst,
+                      const int32_t* w, bool device_input, cudaStream_t s) {
+  DevGraph& d = g->d;
+  if (!d.lsoff || d.L <= 0)
+    NURI_FAIL(NURI_ERR_INVALID,
+              "nuri_set_edge_weights: the graph was loaded without labels (or with "
+              "NURI_LOAD_NO_ISO): edge-weighted isomorphism needs its label segments");
+  const int32_t n = d.n, L = d.L;
+  const int64_t nnz = d.nnz;
+  DBuf<int32_t> ds, dd, dw;
+  const int32_t *ps = src, *pd = dst, *pw = w;
+  if (!device_input && m > 0) {
+    ds.alloc(m, s);
+    dd.alloc(m, s);
+    dw.alloc(m, s);
+    NURI_CUDA(cudaMemcpyAsync(ds.p, src, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
+    NURI_CUDA(cudaMemcpyAsync(dd.p, dst, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
+    NURI_CUDA(cudaMemcpyAsync(dw.p, w, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
+    ps = ds.p;
+    pd = dd.p;
+    pw = dw.p;
+  }
+  DBuf<int32_t> ew, flag;
+  ew.alloc(std::max<int64_t>(nnz, 1), s);
+  flag.alloc(4, s);
+  NURI_CUDA(cudaMemsetAsync(ew.p, 0, sizeof(int32_t) * std::max<int64_t>(nnz, 1), s));
+  NURI_CUDA(cudaMemsetAsync(flag.p, 0, 16, s));
+  if (m > 0)
+    k_ew_scatter<<<blocks_for(m), kThreads, 0, s>>>(g->off.p, g->adj.p, n, ps, pd, pw, m, ew.p,
+                                                    flag.p);
+  NURI_CUDA(cudaGetLastError());
+  int32_t hf[3] = {0, 0, 0};
+  NURI_CUDA(cudaMemcpyAsync(hf, flag.p, 12, cudaMemcpyDeviceToHost, s));
+  NURI_CUDA(cudaStreamSynchronize(s));
+  if (hf[0]) NURI_FAIL(NURI_ERR_INVALID, "nuri_set_edge_weights: vertex id outside [0, n)");
+  if (hf[1]) NURI_FAIL(NURI_ERR_INVALID, "nuri_set_edge_weights: negative weight");
+  if (hf[2]) NURI_FAIL(NURI_ERR_INVALID, "nuri_set_edge_weights: a pair is not an edge of the graph");
+  DBuf<int32_t> emax, lpmax, mx;
+  emax.alloc(std::max<int64_t>((int64_t)n * L, 1), s);
+  lpmax.alloc((int64_t)L * L, s);
+  mx.alloc(1, s);
+  NURI_CUDA(cudaMemsetAsync(emax.p, 0xff, sizeof(int32_t) * std::max<int64_t>((int64_t)n * L, 1), s));
+  NURI_CUDA(cudaMemsetAsync(lpmax.p, 0xff, sizeof(int32_t) * L * L, s));
+  NURI_CUDA(cudaMemsetAsync(mx.p, 0xff, 4, s));
+  DBuf<int2> seg;
+  seg.alloc(std::max<int64_t>(nnz, 1), s);
+  if (nnz > 0) {
+    DBuf<uint64_t> k1, k2;
+    DBuf<int64_t> v1, v2;
+    k1.alloc(nnz, s);
+    k2.alloc(nnz, s);
+    v1.alloc(nnz, s);
+    v2.alloc(nnz, s);
+    k_ew_rows<<<std::max(1, std::min(blocks_for((int64_t)n * 32), sm_count() * 32)), kThreads, 0,
+                s>>>(g->off.p, g->adj.p, g->labels.p, ew.p, n, L, emax.p, k1.p, v1.p);
+    k_ew_labelpairs<<<blocks_for((int64_t)n * L), kThreads, 0, s>>>(g->labels.p, emax.p, n, L,
+                                                                    lpmax.p);
+    k_max_i32<<<blocks_for(nnz), kThreads, 0, s>>>(ew.p, nnz, mx.p);
+    const int end_bit = 32 + bitlen((uint64_t)n * (uint64_t)L);
+    size_t tb = 0;
+    cub::DeviceRadixSort::SortPairs(nullptr, tb, k1.p, k2.p, v1.p, v2.p, nnz, 0, end_bit, s);
+    DBuf<uint8_t> tmp;
+    tmp.alloc(tb, s);
+    NURI_CUDA(cub::DeviceRadixSort::SortPairs(tmp.p, tb, k1.p, k2.p, v1.p, v2.p, nnz, 0, end_bit,
+                                              s));
+    k_ew_segments<<<blocks_for(nnz), kThreads, 0, s>>>(v2.p, nnz, g->adj.p, ew.p, seg.p);
+    NURI_CUDA(cudaGetLastError());
+  }
+  int32_t hmax = -1;
+  NURI_CUDA(cudaMemcpyAsync(&hmax, mx.p, 4, cudaMemcpyDeviceToHost, s));
+  NURI_CUDA(cudaStreamSynchronize(s));
+  g->ew = std::move(ew);
+  g->emax = std::move(emax);
+  g->lpmax = std::move(lpmax);
+  g->lseg_e = std::move(seg);
+  g->h_ewmax = std::max(hmax, 0);
+  d.ew = g->ew.p;
+  d.emax = g->emax.p;
+  d.lpmax = g->lpmax.p;
+  d.lseg_e = g->lseg_e.p;
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -5,6 +5,10 @@
 //   u(s)       = sum over unmatched query vertices q of index(mu(root), label(q), hop(q)),
 //                index = hop/label max index built at load time (Listing 3, cumulative hops);
 //                hops beyond the resident index use the per-label global maximum
+//   edge ranking (Section 2's cumulative edge weight): score(s) = sum of the weights of the
+//                image's edges; u(s) = for every unmatched query edge, the heaviest edge its
+//                images could use (from a matched image: that image's heaviest edge to the
+//                other end's label; else the heaviest edge between the two labels)
 //   dominated  = score + u < tau (strict), tau = k-th best score found so far (per query)
 //   expandable = the added data vertex keeps the partial subgraph isomorphic to the matched
 //                part of the query (label, injectivity, every query edge to a matched vertex)
@@ -39,6 +43,7 @@
 #include <vector>
 
 #include "nuri_internal.cuh"
+#include "topk_common.cuh"
 
 namespace nuri {
 namespace {
@@ -84,7 +89,11 @@ struct IsoCtx {
   const int2* seg;          // weight- or degree-ranked label segments
   const int32_t* idx;       // hop index (nullptr when H == 0)
   const int32_t* gmax;      // per-label global maxima
-  const int32_t* vscore;    // score of a vertex (weights or degrees)
+  const int32_t* vscore;    // score of a vertex (weights or degrees; unused by edge ranking)
+  const int32_t* ew;        // edge ranking: weight of every CSR entry
+  const int32_t* emax;      // edge ranking: [n*L] heaviest edge from a vertex to a label
+  const int32_t* lpmax;     // edge ranking: [L*L] heaviest edge between two labels
+  int32_t edge;             // 1: rank by cumulative edge weight (seg = edge-weight segments)
   const IsoQuery* qs;
   IsoState* st;
   int32_t* hist;            // [nqueries][NBINS]
@@ -118,6 +127,46 @@ __device__ __forceinline__ bool row_contains(const DevGraph& g, int32_t a, int32
   return lo < ea && __ldg(g.adj + lo) == x;
 }
 
+// Edge ranking: the weight of the edge {a, b}, or -1 when a and b are not adjacent (the
+// shorter row is searched; both directions of an edge carry its weight).
+__device__ __forceinline__ int32_t row_weight(const IsoCtx& cx, int32_t a, int32_t b) {
+  const DevGraph& g = cx.g;
+  int64_t ra = g.off[a], ea = g.off[a + 1], rb = g.off[b], eb = g.off[b + 1];
+  int32_t x = b;
+  if (eb - rb < ea - ra) {
+    ra = rb;
+    ea = eb;
+    x = a;
+  }
+  int64_t lo = ra, hi = ea;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (__ldg(g.adj + mid) < x) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo < ea && __ldg(g.adj + lo) == x ? __ldg(cx.ew + lo) : -1;
+}
+
+// Edge ranking: an upper bound of the weights of the query edges from position p to the
+// positions before it, when the positions below m are matched (images mu): an edge to a
+// matched image weighs at most that image's heaviest edge to label(p), any other edge at most
+// the heaviest edge between the two labels.  NONE when such an edge cannot exist.
+__device__ __forceinline__ long long edge_bound(const IsoCtx& cx, const IsoQuery& Q,
+                                                const int32_t* mu, int p, int m) {
+  const int L = cx.g.L;
+  uint32_t pred = Q.back[p] | (1u << Q.ppos[p]);
+  long long t = 0;
+  while (pred) {
+    const int a = __ffs(pred) - 1;
+    pred &= pred - 1;
+    const int32_t x = a < m ? __ldg(cx.emax + (int64_t)mu[a] * L + Q.lab[p])
+                            : __ldg(cx.lpmax + Q.lab[a] * L + Q.lab[p]);
+    if (x < 0) return NONE;
+    t += x;
+  }
+  return t;
+}
+
 __device__ __forceinline__ long long index_value(const IsoCtx& cx, int32_t v, int32_t hop,
                                                  int32_t lab) {
   if (cx.idx && hop <= cx.g.H)
@@ -130,8 +179,9 @@ __device__ void refresh_tau(const IsoCtx& cx, int q, int64_t k, int32_t shift) {
   const int lane = threadIdx.x & 31;
   const int32_t* h = cx.hist + (int64_t)q * NBINS;
   IsoState* S = cx.st + q;
-  int32_t top = *(volatile int32_t*)&S->hmax;
-  long long tau = ld_volatile64(&S->tau);
+  // the loop below is warp-wide: its bounds must be the same in every lane
+  const int32_t top = warp_load(&S->hmax);
+  const long long tau = warp_load(&S->tau);
   int32_t floor_bin = tau < 0 ? 0 : (int32_t)(tau >> shift);
   long long acc = 0;
   for (int32_t b0 = top; b0 >= floor_bin; b0 -= 32) {
@@ -170,9 +220,9 @@ __global__ void k_iso_seeds(IsoCtx cx, int32_t q, int64_t base, int64_t count, i
       keys[base + i] = NONE;
       continue;
     }
-    long long b = __ldg(cx.vscore + v);
+    long long b = cx.edge ? 0 : __ldg(cx.vscore + v);
     for (int p = 1; p < Q.nq; ++p) {
-      long long x = index_value(cx, v, Q.hop[p], Q.lab[p]);
+      long long x = cx.edge ? edge_bound(cx, Q, &v, p, 1) : index_value(cx, v, Q.hop[p], Q.lab[p]);
       if (x < 0) {
         b = NONE;
         break;
@@ -229,8 +279,13 @@ __global__ void k_iso_chunk_write(IsoCtx cx, const long long* __restrict__ keys,
         const int64_t so = (int64_t)v * cx.g.L + Q.lab[1];
         const int64_t at = cx.g.lsoff[so] + j * kSeedChunk;
         if (at < cx.g.lsoff[so + 1]) {
-          // replace position 1's index bound by the chunk's largest candidate score
-          key = key - index_value(cx, v, Q.hop[1], Q.lab[1]) + (long long)__ldg(cx.seg + at).y;
+          // replace position 1's bound by the chunk's largest candidate score (edge ranking:
+          // the weight of the chunk's heaviest edge from the root; position 1 has no other
+          // edge to an earlier position)
+          const long long first =
+              cx.edge ? (long long)__ldg(cx.emax + (int64_t)v * cx.g.L + Q.lab[1])
+                      : index_value(cx, v, Q.hop[1], Q.lab[1]);
+          key = key - first + (long long)__ldg(cx.seg + at).y;
         } else {
           key = NONE;  // an empty segment: the item finds nothing
         }
@@ -268,7 +323,7 @@ __device__ void add_results_leaf(const IsoCtx& cx, int q, const IsoQuery& Q, boo
   __syncwarp();
   __threadfence_block();
   // tau stays "none" until k results exist
-  if ((int64_t)*(volatile unsigned long long*)&S->res_count < (int64_t)Q.k) return;
+  if ((int64_t)warp_load(&S->res_count) < (int64_t)Q.k) return;
   refresh_tau(cx, q, Q.k, Q.shift);
   (void)lane;
 }
@@ -298,7 +353,7 @@ __global__ void __launch_bounds__(ISO_WARPS * 32) k_iso_search(IsoCtx cx,
     int32_t v = (int32_t)(pv & 0x7FFFFFFFull);
     const int64_t chunk = (int64_t)((pv >> 31) & kItemChunkMask);
     IsoState* S = cx.st + q;
-    long long tau = ld_volatile64(&S->tau);
+    long long tau = warp_load(&S->tau);
     if (bound == NONE || bound < tau) {
       if (lane == 0) ++my_pruned;
       continue;
@@ -306,19 +361,30 @@ __global__ void __launch_bounds__(ISO_WARPS * 32) k_iso_search(IsoCtx cx,
     const IsoQuery& Q = cx.qs[q];
     const int nq = Q.nq;
     if (lane == 0) ++my_deq;
-    // rest[i] = sum over positions > i of the index bound (fixed by the root image)
-    long long rest[QMAX];
-    {
+    // rest[i] = sum over positions > i of the index bound (fixed by the root image).  Edge
+    // ranking: rest[i] bounds the edges of the positions after i, bk[i] the back edges of
+    // position i itself (both set when position i is reached, from the images matched then)
+    long long rest[QMAX], bk[QMAX], sx[QMAX];
+    int32_t mu[QMAX];
+    long long sc[QMAX + 1];
+    mu[0] = v;
+    if (cx.edge) {
+      long long acc = 0;
+      for (int p = 2; p < nq; ++p) {
+        const long long x = edge_bound(cx, Q, mu, p, 1);
+        acc = (x < 0 || acc < 0) ? NONE : acc + x;
+      }
+      rest[1] = acc;
+      bk[1] = 0;  // position 1's only earlier position is its parent
+      sc[1] = 0;
+    } else {
       long long acc = 0;
       for (int p = nq - 1; p >= 0; --p) {
         rest[p] = acc;
         if (p >= 1) acc += index_value(cx, v, Q.hop[p], Q.lab[p]);
       }
+      sc[1] = __ldg(cx.vscore + v);
     }
-    int32_t mu[QMAX];
-    long long sc[QMAX + 1];
-    mu[0] = v;
-    sc[1] = __ldg(cx.vscore + v);
     if (nq == 1) {
       // the seed is a complete match
       bool valid = lane == 0 && sc[1] >= tau;
@@ -343,16 +409,17 @@ __global__ void __launch_bounds__(ISO_WARPS * 32) k_iso_search(IsoCtx cx,
           --lev;
           continue;
         }
-        if ((++steps & 255) == 0 && global_ns() > *(const volatile uint64_t*)cx.deadline) {
+        if ((++steps & 255) == 0 && warp_past(cx.deadline)) {
           if (lane == 0) atomicOr(cx.err, 4);
           break;
         }
-        tau = ld_volatile64(&S->tau);
+        tau = warp_load(&S->tau);
         int64_t i = pos[lev] + lane;
         bool in = i < end[lev];
         int2 c = in ? __ldg(cx.seg + i) : make_int2(-1, -1);
         long long s_new = sc[lev] + (long long)c.y;
-        bool okb = in && (s_new + rest[lev] >= tau);
+        // candidates come in descending c.y: this bound falls along the segment
+        bool okb = in && (s_new + (cx.edge ? bk[lev] : 0) + rest[lev] >= tau);
         bool valid = okb;
         if (valid)
           for (int a = 0; a < lev; ++a)
@@ -376,7 +443,13 @@ __global__ void __launch_bounds__(ISO_WARPS * 32) k_iso_search(IsoCtx cx,
           while (m && valid) {
             int a = __ffs(m) - 1;
             m &= m - 1;
-            valid = row_contains(g, mu[a], c.x);
+            if (cx.edge) {  // the back edge's weight joins the score
+              const int32_t wb = row_weight(cx, mu[a], c.x);
+              valid = wb >= 0;
+              s_new += wb;
+            } else {
+              valid = row_contains(g, mu[a], c.x);
+            }
           }
           // induced matching: no data edge where the query has none
           m = Q.nonadj[lev];
@@ -385,6 +458,11 @@ __global__ void __launch_bounds__(ISO_WARPS * 32) k_iso_search(IsoCtx cx,
             m &= m - 1;
             valid = !row_contains(g, mu[a], c.x);
           }
+        }
+        if (cx.edge) {
+          // the exact score (tree and back edges) against tau; kept for the descent
+          if (valid && s_new + rest[lev] < tau) valid = false;
+          sx[lev] = s_new;
         }
         unsigned inm = __ballot_sync(FULL, in);
         unsigned okm = __ballot_sync(FULL, okb);
@@ -410,16 +488,44 @@ __global__ void __launch_bounds__(ISO_WARPS * 32) k_iso_search(IsoCtx cx,
       mask[lev] &= mask[lev] - 1;
       int2 c = __ldg(cx.seg + base[lev] + b);
       long long s_new = sc[lev] + (long long)c.y;
-      tau = ld_volatile64(&S->tau);
-      if (s_new + rest[lev] < tau) {  // tau rose: this and every later candidate fail
+      long long s_exact = 0;  // edge ranking: the candidate's exact score, from its lane
+      if (cx.edge) s_exact = __shfl_sync(FULL, sx[lev], b);
+      tau = warp_load(&S->tau);
+      if (s_new + (cx.edge ? bk[lev] : 0) + rest[lev] < tau) {
+        // tau rose: this and every later candidate fail
         mask[lev] = 0;
         pos[lev] = end[lev];
         continue;
       }
+      if (cx.edge) {
+        if (s_exact + rest[lev] < tau) continue;  // this candidate only
+        s_new = s_exact;
+      }
       mu[lev] = c.x;
       sc[lev + 1] = s_new;
       ++lev;
-      if (Q.refine && lev + 1 < nq) {
+      if (cx.edge) {
+        // bounds of the new level from the images matched so far (positions < lev): lane p
+        // takes the edges of position p > lev
+        long long term = 0;
+        if (lane > lev && lane < nq) term = edge_bound(cx, Q, mu, lane, lev);
+        const bool none = __any_sync(FULL, term < 0);
+        for (int o = 16; o; o >>= 1) term += __shfl_xor_sync(FULL, term, o);
+        rest[lev] = none ? NONE : term;
+        long long kb = 0;
+        uint32_t m = Q.back[lev];
+        while (m) {
+          const int a = __ffs(m) - 1;
+          m &= m - 1;
+          const int32_t x = __ldg(cx.emax + (int64_t)mu[a] * g.L + Q.lab[lev]);
+          if (x < 0) {
+            kb = NONE;
+            break;
+          }
+          kb += x;
+        }
+        bk[lev] = kb;
+      } else if (Q.refine && lev + 1 < nq) {
         // rest[lev] = sum over the positions after lev of the smallest index bound any
         // matched position gives (each is a valid bound: the image lies within the query
         // distance, as a walk, of that matched image); lane p computes position p
@@ -703,8 +809,14 @@ void topk_iso_batch(nuri_graph* G, int32_t nqueries, const nuri_query* qs, const
   const DevGraph& g = G->d;
   DevTimer timer(s);
   const bool deg = rank == NURI_RANK_DEGREE_SUM;
+  const bool edge = rank == NURI_RANK_EDGE_WEIGHT_SUM;
   const bool keep_ties = flags & NURI_KEEP_TIES;
-  const std::vector<int32_t>& gmax = deg ? G->h_gmax_d : G->h_gmax_w;
+  if (edge && !g.ew) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_iso: graph has no edge weights");
+  if (rank == NURI_RANK_WEIGHT_SUM && !g.weights)
+    NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_iso: graph has no weights");
+  const std::vector<int32_t> no_vertex_scores(std::max(g.L, 1), 0);
+  const std::vector<int32_t>& gmax =
+      edge ? no_vertex_scores : (deg ? G->h_gmax_d : G->h_gmax_w);
   int64_t launches = 0;
   if (nqueries >= (1 << (64 - kItemQShift)))
     NURI_FAIL(NURI_ERR_LIMIT, "nuri_topk_iso: at most %d queries in one batch",
@@ -713,6 +825,15 @@ void topk_iso_batch(nuri_graph* G, int32_t nqueries, const nuri_query* qs, const
   for (int i = 0; i < nqueries; ++i)
     if (!prepare_query(qs[i], ks[i], gmax, g.L, (flags & NURI_ISO_INDUCED) != 0, &prep[i]))
       NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_iso: query %d is not a connected simple graph", i);
+  if (edge)
+    for (auto& pq : prep) {
+      // histogram resolution from the largest edge-weight sum a match can have
+      const int64_t mx = (int64_t)pq.q.ne * std::max(G->h_ewmax, 0);
+      int shift = 0;
+      while ((mx >> shift) >= NBINS) ++shift;
+      pq.q.shift = shift;
+      pq.maxscore = mx;
+    }
 
   DBuf<IsoQuery> dq;
   dq.alloc(nqueries, s);
@@ -734,10 +855,14 @@ void topk_iso_batch(nuri_graph* G, int32_t nqueries, const nuri_query* qs, const
   IsoCtx cx;
   memset(&cx, 0, sizeof(cx));
   cx.g = g;
-  cx.seg = deg ? g.lseg_d : g.lseg_w;
-  cx.idx = deg ? g.idx_d : g.idx_w;
-  cx.gmax = deg ? g.gmax_d : g.gmax_w;
-  cx.vscore = deg ? g.deg : g.weights;
+  cx.seg = edge ? g.lseg_e : (deg ? g.lseg_d : g.lseg_w);
+  cx.idx = edge ? nullptr : (deg ? g.idx_d : g.idx_w);
+  cx.gmax = edge ? nullptr : (deg ? g.gmax_d : g.gmax_w);
+  cx.vscore = edge ? nullptr : (deg ? g.deg : g.weights);
+  cx.ew = g.ew;
+  cx.emax = g.emax;
+  cx.lpmax = g.lpmax;
+  cx.edge = edge ? 1 : 0;
   cx.qs = dq.p;
 
   DBuf<long long> keys, keys2;

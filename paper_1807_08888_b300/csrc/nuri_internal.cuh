@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -20,9 +21,14 @@ struct Err {
   nuri_status code;
 };
 
+// Source line of the last CUDA call made through NURI_CUDA (any thread): read only by the
+// query watchdog's report.
+extern std::atomic<int> g_cuda_site;
+
 // Throws Err on a CUDA failure; every C entry point catches and converts to a status.
 #define NURI_CUDA(call)                                                                    \
   do {                                                                                    \
+    ::nuri::g_cuda_site.store(__LINE__, std::memory_order_relaxed);                       \
     cudaError_t e_ = (call);                                                              \
     if (e_ != cudaSuccess) {                                                              \
       ::nuri::set_error("CUDA error %s at %s:%d: %s", cudaGetErrorName(e_), __FILE__,     \
@@ -119,6 +125,14 @@ struct DevGraph {
   const int64_t* lab_off = nullptr; // [L+1] vertices grouped by label
   const int32_t* lab_vert = nullptr;// [n]   (ascending id inside a label)
   int32_t H = 0;
+  // edge weights (nuri_set_edge_weights): ew[t] = weight of CSR entry t (both directions of an
+  // edge hold the same value); emax[v*L + l] = largest weight of an edge from v to a neighbour
+  // of label l (-1: none); lpmax[a*L + b] = largest weight of an edge between labels a and b
+  // (-1: none); lseg_e: the label segments (same lsoff) as {id, w(v, id)}, weight descending
+  const int32_t* ew = nullptr;
+  const int32_t* emax = nullptr;
+  const int32_t* lpmax = nullptr;
+  const int2* lseg_e = nullptr;
 };
 
 }  // namespace nuri
@@ -138,11 +152,15 @@ struct nuri_graph {
   std::vector<int32_t> h_gmax_w, h_gmax_d;  // host copies of the per-label maxima
   std::vector<int64_t> h_lab_off;           // host copy of lab_off
   nuri::DBuf<int2> lseg_w, lseg_d;
+  nuri::DBuf<int32_t> ew, emax, lpmax;  // edge weights and their maxima
+  nuri::DBuf<int2> lseg_e;
+  int32_t h_ewmax = -1;                 // largest edge weight (-1: no edge weights set)
   int64_t device_bytes() const {
     return off.bytes() + ooff.bytes() + lsoff.bytes() + adj.bytes() + deg.bytes() +
            oout.bytes() + vert_of.bytes() + rank_of.bytes() + weights.bytes() + idx_w.bytes() +
            idx_d.bytes() + gmax_w.bytes() + gmax_d.bytes() + labels.bytes() + lseg_w.bytes() +
-           lseg_d.bytes() + lab_off.bytes() + lab_vert.bytes() + core_bits.bytes();
+           lseg_d.bytes() + lab_off.bytes() + lab_vert.bytes() + core_bits.bytes() +
+           ew.bytes() + emax.bytes() + lpmax.bytes() + lseg_e.bytes();
   }
 };
 
@@ -164,12 +182,21 @@ void build_graph(nuri_graph* g, int32_t n, int64_t m, const int32_t* src, const 
                  const uint8_t* labels, const int32_t* weights, int32_t index_hops,
                  uint32_t flags, cudaStream_t s);
 
+// edge weights of a loaded graph (graph_build.cu): m pairs (src, dst) with weight w >= 0, on
+// the host or (device_input) on the device; every pair must be an edge of the graph
+void set_edge_weights(nuri_graph* g, int64_t m, const int32_t* src, const int32_t* dst,
+                      const int32_t* w, bool device_input, cudaStream_t s);
+
 // result packing (capi.cu)
 nuri_result* new_result(int kind, int32_t count, int64_t nverts, int64_t nedges, bool labels);
 
 // cliques.cu
 void topk_cliques(nuri_graph* g, int32_t k, uint32_t flags, int64_t frontier_cap,
                   cudaStream_t s, nuri_result** out);
+
+// wcliques.cu: cliques ranked by cumulative vertex weight, and its device memory bound
+void topk_wcliques(nuri_graph* g, int32_t k, uint32_t flags, cudaStream_t s, nuri_result** out);
+int64_t wclique_query_bytes(const nuri_graph* g, int32_t k);
 
 // device bytes one clique query may allocate, and the local memory of the clique kernels
 int64_t clique_query_bytes(const nuri_graph* g, int32_t k, uint32_t flags, int64_t frontier_cap);

@@ -31,6 +31,7 @@
 #include <vector>
 
 #include "nuri_internal.cuh"
+#include "topk_common.cuh"
 
 namespace nuri {
 namespace {
@@ -206,7 +207,8 @@ __global__ void __launch_bounds__(256) k_mni_exist(MniCtx cx, const Item* __rest
     Item I = items[it];
     const PatDev& P = cx.pats[I.pat];
     uint32_t* Di = cx.bits + (int64_t)(P.dom + I.i) * cx.words;
-    if ((*(volatile uint32_t*)(Di + (I.u >> 5)) >> (I.u & 31)) & 1u) {
+    // other warps set domain bits meanwhile: one reading for the warp
+    if ((warp_load(Di + (I.u >> 5)) >> (I.u & 31)) & 1u) {
       if (lane == 0) ++n_skip;
       continue;
     }
@@ -234,7 +236,7 @@ __global__ void __launch_bounds__(256) k_mni_exist(MniCtx cx, const Item* __rest
           --lev;
           continue;
         }
-        if ((++steps & 255) == 0 && global_ns() > *(const volatile uint64_t*)cx.deadline) {
+        if ((++steps & 255) == 0 && warp_past(cx.deadline)) {
           if (lane == 0) atomicOr(cx.err, 4);
           stop = true;
           break;

@@ -71,7 +71,9 @@ double now_ms() {
 // device memory a request may hold while it runs: the upper bound of every buffer its query
 // allocates (nuri_request_bytes)
 int64_t nuri::request_bytes(const nuri_graph* g, const nuri_request& r) {
-  if (r.kind == NURI_REQ_CLIQUES) return clique_query_bytes(g, r.k, r.flags, 0);
+  if (r.kind == NURI_REQ_CLIQUES)
+    return r.rank == NURI_RANK_WEIGHT_SUM ? wclique_query_bytes(g, r.k)
+                                          : clique_query_bytes(g, r.k, r.flags, 0);
   return iso_query_bytes(g, r.k);
 }
 
@@ -106,6 +108,7 @@ void worker_main(nuri_server* S, int slot) {
             for (auto jt = S->pending.begin();
                  jt != S->pending.end() && (int)batch.size() < S->cfg.max_batch;) {
               if (jt->r.kind == NURI_REQ_CLIQUES && jt->r.flags == batch[0].r.flags &&
+                  jt->r.rank == batch[0].r.rank &&
                   S->fixed_bytes + S->mem_in_use + std::max(mem, jt->mem) <=
                       S->cfg.mem_budget_bytes) {
                 mem = std::max(mem, jt->mem);

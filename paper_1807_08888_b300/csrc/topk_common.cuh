@@ -14,6 +14,29 @@ __device__ __forceinline__ unsigned long long ld_volatile(const unsigned long lo
   return *(const volatile unsigned long long*)p;
 }
 
+// One value for the whole warp: lane 0 loads, the others take its value.  Warp-wide code
+// (shuffles, ballots, __syncwarp with a full mask) may only branch on values every lane
+// agrees on; a location other warps update (a threshold, a domain bitmap, a counter) read by
+// each lane on its own can differ between lanes, which would part the warp before a warp-wide
+// operation that the departed lanes never reach.
+template <class T>
+__device__ __forceinline__ T warp_load(const T* p) {
+  T v{};
+  if ((threadIdx.x & 31) == 0) v = *(const volatile T*)p;
+  return __shfl_sync(0xffffffffu, v, 0);
+}
+
+// The deadline test of warp-wide code, decided by lane 0 for the whole warp.
+__device__ __forceinline__ bool warp_past(const uint64_t* deadline) {
+  int late = 0;
+  if ((threadIdx.x & 31) == 0) {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    late = t > *(const volatile uint64_t*)deadline;
+  }
+  return __shfl_sync(0xffffffffu, late, 0) != 0;
+}
+
 // Threshold from a histogram: tau = max t with sum_{s >= t} hist[s] >= k, or INT32_MIN
 // when fewer than k results exist.  Bins may be coarse (score >> shift): the value returned
 // is then the lower edge of the bin, still a valid lower bound of the exact k-th score.

@@ -144,7 +144,7 @@ def test_forced_spill_equals_resident(monkeypatch):
     assert b.stats["spilled"] > 0 and b.stats["reloaded"] > 0
 
 
-@pytest.mark.parametrize("split", [2, 5, 16])
+@pytest.mark.parametrize("split", [5, 16])
 def test_split_tier_vs_oracle(monkeypatch, split):
     monkeypatch.setenv("NURI_SPLIT_ABOVE", str(split))
     for g in (synth.rmat(10, 8, seed=1), synth.er_small(120, 0.5, seed=78)):
@@ -230,6 +230,34 @@ def test_edge_cases():
         nuri.load_graph(2, np.array([0], np.int32), np.array([5], np.int32))
     with pytest.raises(nuri.NuriError):
         nuri.topk_cliques(G, 0)
+
+
+@pytest.mark.parametrize("case", ["er", "clique_path", "rmat16", "rmat17", "chunglu100k"])
+def test_peel_order_reaches_the_degeneracy(case):
+    # The clique orientation ranks vertices by the batch-peeling (core decomposition) order;
+    # its largest out-degree equals the graph's degeneracy, the largest core number, which
+    # networkx computes independently.  Graphs of at most 65536 vertices are peeled wholly by
+    # the one-CTA tail kernel; the larger ones start in the multi-launch loop and hand a
+    # non-empty front over to it (rmat17's hubs also take the tail's whole-CTA row path).
+    nx = pytest.importorskip("networkx")
+    if case == "er":
+        g = synth.er_small(300, 0.1, seed=1)
+    elif case == "clique_path":
+        c = list(itertools.combinations(range(40), 2)) + [(i, i + 1) for i in range(39, 399)]
+        e = np.array(c, np.int32)
+        g = synth.Graph(400, e[:, 0].copy(), e[:, 1].copy())
+    elif case == "rmat16":
+        g = synth.rmat(16, 16, seed=3)
+    elif case == "rmat17":
+        g = synth.rmat(17, 16, seed=4)
+    else:
+        g = synth.chung_lu_planted(100_000, 20.0, 2.1, 10, 8, 16, seed=7)
+    G = load(g)
+    H = nx.Graph()
+    H.add_nodes_from(range(g.n))
+    H.add_edges_from((int(a), int(b)) for a, b in zip(g.src, g.dst) if a != b)
+    expect = max(nx.core_number(H).values()) if g.n else 0
+    assert G.info()["max_out_degree"] == expect
 
 
 def test_clique_limit_is_reported():

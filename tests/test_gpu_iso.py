@@ -230,3 +230,104 @@ def test_matched_vertex_bound_same_rows_fewer_candidates(monkeypatch):
     for q, a, b in zip(qs, tight, loose):
         assert grows(a) == grows(b) == orows(g, q, 100), q
     assert tight[0].stats["expansions"] <= loose[0].stats["expansions"]
+
+
+def _edge_weighted(g, seed, hi=100, dup=True):
+    """One weight per input pair (uniform 0..hi); with dup, a third of the pairs come once
+    more, reversed, with their own weight (an edge weighs the larger)."""
+    rng = np.random.default_rng(seed)
+    if dup and g.m:
+        pick = rng.integers(0, g.m, size=max(1, g.m // 3))
+        g.src, g.dst = (np.concatenate([g.src, g.dst[pick]]).astype(np.int32),
+                        np.concatenate([g.dst, g.src[pick]]).astype(np.int32))
+    g.edge_weights = rng.integers(0, hi + 1, size=g.m).astype(np.int32)
+    return g
+
+
+def load_ew(g, hops=2):
+    G = load(g, hops)
+    G.set_edge_weights(g.src, g.dst, g.edge_weights)
+    return G
+
+
+def orows_e(g, q, k, induced=False):
+    return [(r[0], tuple(r[1]), tuple(r[2]))
+            for r in oracle.topk_iso(g, q, k, induced=induced, edge_rank=True)]
+
+
+def test_edge_rank_tiny_vs_oracle_and_brute():
+    """Ranking by cumulative edge weight (NURI_RANK_EDGE_WEIGHT_SUM) on tiny labelled graphs:
+    the CUDA rows equal the oracle's and brute force's, non-induced and induced."""
+    rng = np.random.default_rng(17)
+    for i in range(30):
+        g = _edge_weighted(_labelled(int(rng.integers(2, 12)), [0.3, 0.5, 0.8][i % 3], 1700 + i),
+                           seed=i, hi=[3, 40][i % 2])
+        G = load_ew(g, hops=int(rng.integers(0, 3)))
+        for q in _shapes(rng, 3, sizes=(1, 2, 3, 4, 6)):
+            for induced in (False, True):
+                every = [tuple(r) for r in brute.topk_iso(g, q, 10 ** 9, induced=induced,
+                                                          edge_rank=True)]
+                for k in (1, 5, 100):
+                    got = grows(nuri.topk_iso(G, q, k, induced=induced, edge_rank=True))
+                    assert got == every[:k], (g.name, q, k, induced)
+                    assert orows_e(g, q, k, induced) == every[:k]
+
+
+@pytest.mark.parametrize("scale", [10, 12])
+def test_edge_rank_rmat_vs_oracle(scale):
+    """R-MAT 10 / 12 with 8 labels and edge weights 0..1000: queries of 3 to 8 vertices
+    (every shape), k up to 1000, one batched launch and one query at a time."""
+    g = _edge_weighted(_rmat_labelled(scale, 16, seed=60 + scale), seed=scale, hi=1000)
+    G = load_ew(g)
+    rng = np.random.default_rng(70 + scale)
+    qs = [synth.random_query(rng, kind, s, 8)
+          for kind in ("path", "cycle", "star", "tree") for s in (3, 5, 8)]
+    ks = [1, 10, 100, 1000] * 3
+    batch = nuri.topk_iso_batch(G, qs, ks, edge_rank=True)
+    for q, k, b in zip(qs, ks, batch):
+        want = orows_e(g, q, k)
+        assert grows(b) == want, (q, k)
+        assert grows(nuri.topk_iso(G, q, k, edge_rank=True)) == want, (q, k)
+    # the same graph still ranks by vertex weight when asked
+    q = qs[1]
+    assert grows(nuri.topk_iso(G, q, 10)) == orows(g, q, 10)
+
+
+def test_edge_rank_inputs_and_errors():
+    torch = pytest.importorskip("torch")
+    g = _edge_weighted(_rmat_labelled(10, 8, seed=81, nlab=4), seed=3, hi=50, dup=False)
+    G = load(g)
+    q = synth.cycle_query([0, 1, 2])
+    with pytest.raises(nuri.NuriError):  # no edge weights yet
+        nuri.topk_iso(G, q, 5, edge_rank=True)
+    # device tensors give the same weights as host arrays
+    G.set_edge_weights(torch.from_numpy(g.src).cuda(), torch.from_numpy(g.dst).cuda(),
+                       torch.from_numpy(g.edge_weights).cuda())
+    assert grows(nuri.topk_iso(G, q, 50, edge_rank=True)) == orows_e(g, q, 50)
+    # a pair that is not an edge, a negative weight, an id out of range: rejected, and the
+    # weights set before stay in use
+    adj = {(int(a), int(b)) for a, b in zip(g.src, g.dst)} | \
+        {(int(b), int(a)) for a, b in zip(g.src, g.dst)}
+    non = next((a, b) for a in range(g.n) for b in range(a + 1, g.n) if (a, b) not in adj)
+    for s, d, w in ((non[0], non[1], 1), (int(g.src[0]), int(g.dst[0]), -1), (0, g.n, 1)):
+        with pytest.raises(nuri.NuriError) as ei:
+            G.set_edge_weights(np.array([s], np.int32), np.array([d], np.int32),
+                               np.array([w], np.int32))
+        assert ei.value.code == nuri.ERR_INVALID
+    assert grows(nuri.topk_iso(G, q, 50, edge_rank=True)) == orows_e(g, q, 50)
+    # edges given no weight weigh 0: weighting only the first pair
+    G.set_edge_weights(g.src[:1], g.dst[:1], np.array([7], np.int32))
+    top = nuri.topk_iso(G, synth.path_query([int(g.labels[g.src[0]]), int(g.labels[g.dst[0]])]),
+                        1, edge_rank=True)
+    if g.src[0] != g.dst[0]:
+        assert top[0][0] == 7
+    # mixed batch: the same query ranked three ways
+    G.set_edge_weights(g.src, g.dst, g.edge_weights)
+    outs = nuri.topk_batch(G, [("iso", q, 20), ("iso", q, 20, "edge"), ("iso", q, 20, True)])
+    assert grows(outs[1]) == orows_e(g, q, 20)
+    assert grows(outs[0]) == orows(g, q, 20)
+    assert grows(outs[2]) == orows(g, q, 20, True)
+    # an unlabelled graph has no label segments
+    U = nuri.load_graph(g.n, g.src, g.dst)
+    with pytest.raises(nuri.NuriError):
+        U.set_edge_weights(g.src, g.dst, g.edge_weights)
