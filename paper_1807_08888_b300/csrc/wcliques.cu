@@ -461,6 +461,15 @@ __global__ void k_wcompact(const WRec* __restrict__ in, int64_t n, long long tau
   }
 }
 
+// Slots of the launch output marked empty: a record whose reservation fails still moves the
+// output counter, so slots past the last granted reservation are read by the compaction and
+// must not hold records of an earlier launch.
+__global__ void k_wclear(WRec* __restrict__ recs, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    recs[i].nv = 0;
+}
+
 __global__ void k_wkeys(const WRec* __restrict__ recs, int64_t n, long long* __restrict__ keys,
                         int32_t* __restrict__ idx) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -659,8 +668,12 @@ void topk_wcliques(nuri_graph* G, int32_t k, uint32_t flags, cudaStream_t s,
   deadline.alloc(1, s);
   ++launches;
   k_set_deadline<<<1, 32, 0, s>>>(deadline.p, time_budget_ns());
+  // output slots per launch (a smaller value exercises the hand-back of records in tests)
+  int64_t out_cap = kOutCap;
+  if (const char* e = getenv("NURI_WOUT_CAP"))
+    out_cap = std::max<int64_t>((int64_t)g.max_out + 1, std::min<int64_t>(kOutCap, atoll(e)));
   DBuf<WRec> outb, defer, res;
-  outb.alloc(kOutCap, s);
+  outb.alloc(out_cap, s);
   defer.alloc(kBatch, s);
   int64_t res_cap = std::max<int64_t>(1 << 16, (int64_t)k * 64);
   if (const char* e = getenv("NURI_RESULT_CAP")) res_cap = std::max<int64_t>(1, atoll(e));
@@ -677,7 +690,7 @@ void topk_wcliques(nuri_graph* G, int32_t k, uint32_t flags, cudaStream_t s,
   cx.wr = wr.p;
   cx.hist = hist.p;
   cx.out = outb.p;
-  cx.out_cap = kOutCap;
+  cx.out_cap = out_cap;
   cx.defer = defer.p;
   cx.scratch = scratch.p;
   cx.k = k;
@@ -697,6 +710,8 @@ void topk_wcliques(nuri_graph* G, int32_t k, uint32_t flags, cudaStream_t s,
     hs.tau = tau0;
     NURI_CUDA(cudaMemcpyAsync(st.p, &hs, sizeof(hs), cudaMemcpyHostToDevice, s));
     NURI_CUDA(cudaMemsetAsync(hist.p, 0, sizeof(int32_t) * WBINS, s));
+    ++launches;
+    k_wclear<<<wgrid(out_cap), 256, 0, s>>>(outb.p, out_cap);  // no records of a past pass
     // the stack: seed batches, the best bounds on top
     std::vector<Batch> stack;
     for (int64_t b = ((int64_t)n + kBatch - 1) / kBatch - 1; b >= 0; --b) {
@@ -769,7 +784,7 @@ void topk_wcliques(nuri_graph* G, int32_t k, uint32_t flags, cudaStream_t s,
         NURI_CUDA(cudaMemcpyAsync(x.recs.p, defer.p, sizeof(WRec) * x.n, cudaMemcpyDeviceToDevice, s));
         stack.push_back(std::move(x));
       }
-      const int64_t nout = std::min<int64_t>((int64_t)hs.out_count, kOutCap);
+      const int64_t nout = std::min<int64_t>((int64_t)hs.out_count, out_cap);
       if (nout > 0) {
         // drop empty and dominated slots, then sort by bound descending
         DBuf<WRec> packed;
@@ -778,6 +793,8 @@ void topk_wcliques(nuri_graph* G, int32_t k, uint32_t flags, cudaStream_t s,
         ++launches;
         k_wcompact<<<wgrid(nout * 32), 256, 0, s>>>(outb.p, nout, no_prune ? LLONG_MIN : hs.tau,
                                                     packed.p, cnt.p);
+        ++launches;
+        k_wclear<<<wgrid(nout), 256, 0, s>>>(outb.p, nout);
         unsigned long long np = 0;
         NURI_CUDA(cudaMemcpyAsync(&np, cnt.p, 8, cudaMemcpyDeviceToHost, s));
         NURI_CUDA(cudaStreamSynchronize(s));

@@ -96,3 +96,16 @@ def test_ties_restart_batch_and_errors(monkeypatch):
     U = nuri.load_graph(g.n, g.src, g.dst)
     with pytest.raises(nuri.NuriError):
         nuri.topk_cliques(U, 5, weighted=True)
+
+
+def test_handed_back_records_keep_rows_exact(monkeypatch):
+    """A launch output smaller than a round's children: records whose children do not fit are
+    handed back whole and redone, and output slots past the granted reservations must not
+    bring back records of an earlier launch.  Rows equal the oracle's."""
+    g = _weighted(synth.er_small(200, 0.5, seed=77), 5, 1000)
+    G = load(g)
+    want = {k: orows(g, k) for k in (1, 10, 100)}
+    monkeypatch.setenv("NURI_WOUT_CAP", "150")
+    for k in (1, 10, 100):
+        assert rows(nuri.topk_cliques(G, k, weighted=True)) == want[k], k
+    monkeypatch.delenv("NURI_WOUT_CAP")
