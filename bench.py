@@ -361,7 +361,7 @@ def main():
                    "d2h_bytes_per_step": int(d2h),
                    "includes": "H2D edge list, device CSR build, query, D2H rows"}
     if not args.no_extra and rank == 0:
-        line["workloads"] = extra_workloads(nuri, torch, sptr, G)
+        line["workloads"] = extra_workloads(nuri, torch, sptr, G, g)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.ref_budget)
     if rank == 0:
@@ -534,14 +534,57 @@ def clique_batch_vs_plain(nuri, torch, G, sptr, count=16, seed=5):
             "rows_equal_plain": bool(same)}
 
 
-def extra_workloads(nuri, torch, sptr, G_headline=None):
+def weighted_rankings(nuri, sptr, g_headline):
+    """The weighted rankings: top-100 cliques by vertex weight on the headline graph with
+    weights uniform 0..1000, and 16 isomorphism queries of the R-MAT 20 workload at top-100
+    ranked by edge weight (edge weights uniform 0..1000) next to the same queries ranked by
+    vertex weight.  Device time of the query (CUDA events inside the library), algorithmic
+    bytes from the kernels' counters over that time against the measured copy bandwidth."""
+    import synth
+    hbm = peaks()[0]
+    out = {}
+    if g_headline is not None:
+        w = synth.weights_uniform(g_headline.n, 0, 1000, seed=11)
+        G = nuri.load_graph(g_headline.n, g_headline.src, g_headline.dst, weights=w, stream=sptr)
+        nuri.topk_cliques(G, 100, weighted=True, stream=sptr)  # warm-up
+        r = nuri.topk_cliques(G, 100, weighted=True, stream=sptr)
+        ms = _ms(r)
+        out["chunglu1m_top100_weighted_cliques"] = {
+            "time_to_topk_ms": ms, "expansions": r.stats["expansions"],
+            "expansions_per_s": r.stats["expansions"] / (ms / 1e3),
+            "algorithmic_gbs": r.stats["adj_bytes"] / (ms / 1e3) / 1e9,
+            "hbm_frac_of_measured": r.stats["adj_bytes"] / (ms / 1e3) / 1e9 / hbm,
+            "top_score": r[0][0] if r else None, "launches": r.stats["launches"]}
+        G.free()
+    g = synth.workload("rmat20")
+    g.edge_weights = synth.edge_weights_uniform(g.m, 0, 1000, seed=12)
+    G = nuri.load_graph(g.n, g.src, g.dst, labels=g.labels, weights=g.weights, index_hops=4,
+                        stream=sptr)
+    G.set_edge_weights(g.src, g.dst, g.edge_weights, stream=sptr)
+    qs = synth.query_batch(64, seed=1)[:16]
+    res = {}
+    for name, edge in (("edge_weight", True), ("vertex_weight", False)):
+        nuri.topk_iso_batch(G, qs, [100] * 16, edge_rank=edge, stream=sptr)  # warm-up
+        rb = nuri.topk_iso_batch(G, qs, [100] * 16, edge_rank=edge, stream=sptr)
+        ms = _ms(rb[0])
+        res[name] = {"time_to_topk_ms": ms, "expansions": rb[0].stats["expansions"],
+                     "expansions_per_s": rb[0].stats["expansions"] / (ms / 1e3),
+                     "algorithmic_gbs": rb[0].stats["adj_bytes"] / (ms / 1e3) / 1e9,
+                     "hbm_frac_of_measured": rb[0].stats["adj_bytes"] / (ms / 1e3) / 1e9 / hbm}
+    out["rmat20_iso16_top100_by_edge_weight"] = res
+    G.free()
+    return out
+
+
+def extra_workloads(nuri, torch, sptr, G_headline=None, g_headline=None):
     """The other configurations: clique requests batched vs one at a time on the headline
     graph, ER planted clique, the 64-query isomorphism batch (batched launch vs one query at a
-    time), and pattern mining M = 1..5."""
+    time), pattern mining M = 1..5, and the weighted rankings."""
     import synth
     out = {}
     if G_headline is not None:
         out["chunglu1m_clique_batch16"] = clique_batch_vs_plain(nuri, torch, G_headline, sptr)
+    out.update(weighted_rankings(nuri, sptr, g_headline))
     g = synth.workload("er2000")
     G = nuri.load_graph(g.n, g.src, g.dst, stream=sptr)
     for _ in range(3):
