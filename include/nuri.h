@@ -70,6 +70,12 @@ typedef int32_t nuri_status;
 #define NURI_ISO_INDUCED 0x400u     /* induced matches: non-adjacent query vertices map to
                                        non-adjacent data vertices (Section 2's isomorphism
                                        definition read as "edge if and only if edge")       */
+/* nuri_topk_patterns flags */
+#define NURI_PATTERNS_EDGE_ORIENTED 0x800u /* exhaustive edge-oriented expansion (every connected
+                                       M-edge subgraph grown one edge at a time from one-edge
+                                       subgraphs, grouped by pattern; Section 2's other
+                                       expansion, the Arabesque way): the ablation beside
+                                       Algorithm 2, same rows, no pruning                    */
 
 typedef struct nuri_graph nuri_graph;
 
@@ -228,6 +234,10 @@ nuri_status nuri_topk_iso_batch(nuri_graph* g, int32_t nqueries, const nuri_quer
  * nuri_topk_patterns -- top-k connected vertex-labelled patterns with exactly M edges by
  * minimum image-based support (Algorithm 2, Section 4.2 functions: priority (m, f),
  * dominated = f < f(k-th)).  1 <= M <= 5.
+ *   flags  NURI_KEEP_TIES; NURI_PATTERNS_EDGE_ORIENTED computes the same rows by exhaustive
+ *          edge-oriented expansion (stats.expansions = subgraphs grown, stats.results_stored =
+ *          embeddings, stats.dequeued = distinct patterns); NURI_ERR_LIMIT when more than 4096
+ *          edges touch one subgraph or the embeddings pass 2^28.
  */
 nuri_status nuri_topk_patterns(nuri_graph* g, int32_t M, int32_t k, int32_t rank,
                                uint32_t flags, void* stream, nuri_result** out);

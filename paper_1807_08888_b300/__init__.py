@@ -33,7 +33,7 @@ REQ_CLIQUES, REQ_ISO, REQ_PATTERNS = 0, 1, 2
 RANK_SIZE, RANK_WEIGHT_SUM, RANK_DEGREE_SUM, RANK_MNI, RANK_EDGE_WEIGHT_SUM = range(5)
 LOAD_DEVICE_INPUT, LOAD_NO_ISO = 0x1, 0x2
 CLIQUE_ALL, CLIQUE_MAXIMAL = 0x0, 0x1
-KEEP_TIES, NO_PRUNE, ISO_INDUCED = 0x100, 0x200, 0x400
+KEEP_TIES, NO_PRUNE, ISO_INDUCED, PATTERNS_EDGE_ORIENTED = 0x100, 0x200, 0x400, 0x800
 
 # every function include/nuri.h declares
 EXPORTS = (
@@ -413,9 +413,12 @@ def topk_batch(g: Graph, requests, stream=None) -> list:
     return [_unpack(outs[i]) for i in range(n)]
 
 
-def topk_patterns(g: Graph, M: int, k: int, stream=None) -> Result:
+def topk_patterns(g: Graph, M: int, k: int, stream=None, keep_ties=False,
+                  edge_oriented=False) -> Result:
+    """edge_oriented: exhaustive edge-oriented expansion (the ablation beside Algorithm 2)."""
+    flags = (KEEP_TIES if keep_ties else 0) | (PATTERNS_EDGE_ORIENTED if edge_oriented else 0)
     rp = ctypes.POINTER(_Result)()
-    _check(lib().nuri_topk_patterns(g.handle, int(M), int(k), RANK_MNI, 0, _stream(stream),
+    _check(lib().nuri_topk_patterns(g.handle, int(M), int(k), RANK_MNI, flags, _stream(stream),
                                     ctypes.byref(rp)))
     return _unpack(rp)
 

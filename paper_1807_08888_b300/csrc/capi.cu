@@ -15,6 +15,10 @@
 
 namespace nuri {
 
+// patterns_edge.cu: top-k patterns by exhaustive edge-oriented expansion
+void topk_patterns_edge(nuri_graph* g, int32_t M, int32_t k, uint32_t flags, cudaStream_t s,
+                        nuri_result** out);
+
 static thread_local char g_err[1024] = "";
 
 void set_error(const char* fmt, ...) {
@@ -257,7 +261,8 @@ nuri_status nuri_topk_patterns(nuri_graph* g, int32_t M, int32_t k, int32_t rank
     if (M < 1 || M > 5) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_patterns: M must be 1..5");
     if (rank != NURI_RANK_MNI) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_patterns: rank must be NURI_RANK_MNI");
     if (!g->d.labels || !g->d.lsoff) NURI_FAIL(NURI_ERR_INVALID, "nuri_topk_patterns: graph has no labels");
-    topk_patterns(g, M, k, flags, (cudaStream_t)stream, out);
+    if (flags & NURI_PATTERNS_EDGE_ORIENTED) topk_patterns_edge(g, M, k, flags, (cudaStream_t)stream, out);
+    else topk_patterns(g, M, k, flags, (cudaStream_t)stream, out);
   });
 }
 
@@ -396,7 +401,8 @@ nuri_status nuri_topk_batch(nuri_graph* g, int32_t nreq, const nuri_request* req
           }, outs);
         } else if (r0.kind == NURI_REQ_PATTERNS) {
           run_prefix_group(idx, reqs, r0.flags, [&](int32_t K, uint32_t fl, nuri_result** o) {
-            topk_patterns(g, r0.pattern_edges, K, fl, s, o);
+            if (fl & NURI_PATTERNS_EDGE_ORIENTED) topk_patterns_edge(g, r0.pattern_edges, K, fl, s, o);
+            else topk_patterns(g, r0.pattern_edges, K, fl, s, o);
           }, outs);
         } else {
           std::vector<nuri_query> qs;

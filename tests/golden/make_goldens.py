@@ -163,12 +163,42 @@ def make_patterns_rmat18z(Ms=(1, 2, 3, 4, 5)):
             json.dump(out, f, separators=(",", ":"))
 
 
+# ---- vertex-weighted cliques: R-MAT 11 with weights 0..1000, top-100 ----------------------
+WCLIQUE_CASE = ("rmat", (11, 16), {"seed": 11}, (0, 1000, 211))
+
+
+def wclique_graph():
+    import synth
+    fn, args, kw, (lo, hi, wseed) = WCLIQUE_CASE
+    g = getattr(synth, fn)(*args, **kw)
+    g.weights = synth.weights_uniform(g.n, lo, hi, seed=wseed)
+    return g
+
+
+def make_wcliques_rmat11(k=100):
+    import oracle
+    g = wclique_graph()
+    t = time.time()
+    r = oracle.topk_wcliques(g, k)
+    out = {"case": "wcliques_rmat11_top100", "recipe": [WCLIQUE_CASE[0], list(WCLIQUE_CASE[1]),
+                                                       WCLIQUE_CASE[2], list(WCLIQUE_CASE[3])],
+           "sha256_graph": g.sha256(),
+           "source": "oracle.topk_wcliques (Algorithm 1 with the clique functions, vertex-weight "
+                     "score, bound w(V) + w(P))",
+           "oracle_seconds": time.time() - t,
+           "rows": [[x[0], list(x[1])] for x in r]}
+    with open(os.path.join(HERE, "wcliques_rmat11_top100.json"), "w") as f:
+        json.dump(out, f, separators=(",", ":"))
+    print("wcliques", out["oracle_seconds"], flush=True)
+
+
 CASES = {
     "cliques_er1200": lambda: make_cliques("er1200_p025_s91"),
     "cliques_er1000": lambda: make_cliques("er1000_p033_s5", k_all=300, k_max=100),
     "cliques_chunglu100k": lambda: make_chunglu("chunglu100k"),
     "iso_rmat20": make_iso_rmat20,
     "patterns_rmat18z": make_patterns_rmat18z,
+    "wcliques_rmat11": make_wcliques_rmat11,
 }
 
 if __name__ == "__main__":

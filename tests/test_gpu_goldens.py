@@ -20,7 +20,7 @@ pytestmark = pytest.mark.gpu
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 sys.path.insert(0, GOLD)
 from make_goldens import (CHUNGLU_CASES, CLIQUE_CASES, chunglu_graph, clique_graph,  # noqa: E402
-                          row_digest)
+                          row_digest, wclique_graph)
 
 
 def _golden(name):
@@ -77,6 +77,21 @@ def test_cliques_headline_recipe_vs_bron_kerbosch(case):
     nuri.tune_cliques(G, 100)
     assert [(r[0], r[1]) for r in nuri.topk_cliques(G, 100)] == want
     assert [(r[0], r[1]) for r in nuri.topk_batch(G, [("clique", 100)])[0]] == want
+
+
+def test_weighted_cliques_rmat11_vs_oracle():
+    """Cliques ranked by vertex weight on R-MAT 11 (weights 0..1000): top-100 of Algorithm 1
+    with the weighted bound (48 s in the oracle), row for row, one query and in a batch."""
+    d = _golden("wcliques_rmat11_top100.json")
+    g = wclique_graph()
+    assert g.sha256() == d["sha256_graph"]
+    G = nuri.load_graph(g.n, g.src, g.dst, weights=g.weights)
+    want = [(r[0], tuple(r[1])) for r in d["rows"]]
+    for k in (1, 10, 100):
+        assert [(r[0], r[1]) for r in nuri.topk_cliques(G, k, weighted=True)] == want[:k], k
+    outs = nuri.topk_batch(G, [("clique", 100, False, False, True), ("clique", 7, False, False, True)])
+    assert [(r[0], r[1]) for r in outs[0]] == want
+    assert [(r[0], r[1]) for r in outs[1]] == want[:7]
 
 
 def test_iso_rmat20_sixty_four_queries_vs_oracle():

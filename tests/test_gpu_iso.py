@@ -331,3 +331,16 @@ def test_edge_rank_inputs_and_errors():
     U = nuri.load_graph(g.n, g.src, g.dst)
     with pytest.raises(nuri.NuriError):
         U.set_edge_weights(g.src, g.dst, g.edge_weights)
+
+
+def test_edge_rank_rmat14_batch_vs_oracle():
+    """Sixteen seeded queries (3 to 8 vertices) on R-MAT 14 with 8 labels and edge weights
+    0..1000, top-100 by cumulative edge weight, in one batched launch: every row equal to the
+    oracle's (about 10 s of oracle time)."""
+    g = _rmat_labelled(14, 16, seed=14)
+    g.edge_weights = synth.edge_weights_uniform(g.m, 0, 1000, seed=314)
+    G = load_ew(g)
+    qs = synth.query_batch(16, seed=3, size_lo=3, size_hi=8, num_labels=8)
+    batch = nuri.topk_iso_batch(G, qs, [100] * len(qs), edge_rank=True)
+    for q, b in zip(qs, batch):
+        assert grows(b) == orows_e(g, q, 100), q
