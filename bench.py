@@ -243,8 +243,8 @@ def main():
     ap.add_argument("--ref-budget", type=int, default=30_000_000)
     ap.add_argument("--workload", default="headline",
                     choices=["headline", "serving", "profile-clique", "profile-clique1m",
-                             "profile-iso",
-                             "profile-hop", "profile-patterns"])
+                             "profile-iso", "profile-iso-edge", "profile-wcliques",
+                             "profile-esu", "profile-hop", "profile-patterns"])
     ap.add_argument("--repeat", type=int, default=1,
                     help="profile cases: queries run one after another on the loaded graph")
     ap.add_argument("--serving-graph", default="rmat22")
@@ -252,6 +252,10 @@ def main():
     ap.add_argument("--calibrate", type=int, default=200)
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--request-budget-ms", type=float, default=60000.0)
+    ap.add_argument("--serving-kinds", default="mix", choices=["mix", "iso", "clique"],
+                    help="serving: the 50/50 stream, or only its isomorphism or clique requests "
+                         "(thinned from a stream at twice the rate, so each kind keeps its "
+                         "arrival process)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -404,6 +408,32 @@ def profile_case(which, nuri, sptr, repeat=1):
         for i in range(repeat):
             r = nuri.topk_iso_batch(G, synth.query_batch(64, seed=1), [1000] * 64, stream=sptr)
             print(json.dumps({"case": which, "query": i, "stats": r[0].stats}))
+    elif which == "iso-edge":
+        g = synth.rmat(18, 16, seed=3)
+        g.labels = synth.labels_uniform(g.n, 8, seed=4)
+        g.weights = synth.weights_uniform(g.n, 0, 1000, seed=5)
+        g.edge_weights = synth.edge_weights_uniform(g.m, 0, 1000, seed=6)
+        G = nuri.load_graph(g.n, g.src, g.dst, labels=g.labels, weights=g.weights,
+                            stream=sptr)
+        G.set_edge_weights(g.src, g.dst, g.edge_weights, stream=sptr)
+        for i in range(repeat):
+            r = nuri.topk_iso_batch(G, synth.query_batch(16, seed=1), [100] * 16,
+                                    edge_rank=True, stream=sptr)
+            print(json.dumps({"case": which, "query": i, "stats": r[0].stats}))
+    elif which == "wcliques":
+        g = synth.chung_lu_planted(200000, 20.0, 2.1, 20, 15, 30, seed=0)
+        w = synth.weights_uniform(g.n, 0, 1000, seed=11)
+        G = nuri.load_graph(g.n, g.src, g.dst, weights=w, stream=sptr)
+        for i in range(repeat):
+            r = nuri.topk_cliques(G, 100, weighted=True, stream=sptr)
+            print(json.dumps({"case": which, "query": i, "stats": r.stats}))
+    elif which == "esu":
+        g = synth.rmat(12, 16, seed=41)
+        g.labels = synth.labels_zipf(g.n, 8, 1.2, seed=41)
+        G = nuri.load_graph(g.n, g.src, g.dst, labels=g.labels, stream=sptr)
+        for i in range(repeat):
+            r = nuri.topk_patterns(G, 2, 10, edge_oriented=True, stream=sptr)
+            print(json.dumps({"case": which, "query": i, "stats": r.stats}))
     elif which == "hop":
         g = synth.workload("rmat20")
         G = nuri.load_graph(g.n, g.src, g.dst, labels=g.labels, weights=g.weights,
@@ -433,7 +463,15 @@ def serving(args, nuri, torch, sptr):
             return nuri.topk_cliques(G, r["k"], stream=sptr)
         return nuri.topk_iso(G, r["query"], r["k"], stream=sptr)
 
-    calib = synth.serving_requests(args.calibrate, rate=1.0, seed=100)
+    kinds = args.serving_kinds
+
+    def stream(count, rate, seed):
+        if kinds == "mix":
+            return synth.serving_requests(count, rate=rate, seed=seed)
+        both = synth.serving_requests(2 * count + 256, rate=2 * rate, seed=seed)
+        return [r for r in both if r["kind"] == kinds][:count]
+
+    calib = stream(args.calibrate, 1.0, 100)
     for r in calib[:5]:  # warm-up (a request may hit the per-request time budget)
         try:
             run_alone(r)
@@ -449,10 +487,10 @@ def serving(args, nuri, torch, sptr):
     mu1 = len(calib) / (time.perf_counter() - t0)
     out = {"graph": args.serving_graph, "edges": G.info()["num_edges"], "load_s": load_s,
            "mu1_req_per_s": mu1, "calibration_failures": fails, "slots": args.slots,
-           "requests_per_rate": args.requests, "rates": {}}
+           "requests_per_rate": args.requests, "kinds": kinds, "rates": {}}
     for i, f in enumerate((0.5, 1.0, 2.0)):
         rate = f * mu1
-        reqs = synth.serving_requests(args.requests, rate=rate, seed=i)
+        reqs = stream(args.requests, rate, i)
         srv = nuri.Server(G, slots=args.slots, max_batch=64)
         tickets = [None] * len(reqs)
         start = time.perf_counter()

@@ -457,7 +457,9 @@ def request_bytes(g: Graph, kind, k, query=None, maximal=False) -> int:
 class Server:
     """Continuous-batching request server over a resident graph (nuri_server_*)."""
 
-    def __init__(self, g: Graph, slots=4, max_batch=64, mem_budget_bytes=8 << 30):
+    def __init__(self, g: Graph, slots=4, max_batch=64, mem_budget_bytes=0):
+        """mem_budget_bytes: device memory the server admits requests into (0: the library's
+        default, 80 % of the free device memory at creation)."""
         self._g = g  # keep the graph alive
         cfg = _ServerCfg(int(slots), int(max_batch), int(mem_budget_bytes))
         h = ctypes.c_void_p()
