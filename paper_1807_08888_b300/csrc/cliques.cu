@@ -1818,16 +1818,30 @@ __global__ void k_raise_tau(int32_t* tau, int32_t v) {
   if (threadIdx.x == 0 && blockIdx.x == 0) atomicMax(tau, v);
 }
 
+// Count one into hist[b] for every lane with b >= 0; lanes of a warp with the same bucket
+// (neighbouring keys mostly share one) add together, one atomic per distinct bucket.
+__device__ __forceinline__ void warp_hist_add(int32_t* hist, int b) {
+  const unsigned peers = __match_any_sync(0xffffffffu, b);
+  if (b >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[b], __popc(peers));
+}
+
 __global__ void k_bucket_hist(const int32_t* keys, int64_t n, int32_t* hist) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    atomicAdd(&hist[(keys[i] >> 24) * NB + bucket_of(keys[i] & 0xffffff)], 1);
+  // whole warps step together (the tail lanes pass b = -1)
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x; i0 < n; i0 += stride) {
+    const int64_t i = i0 + threadIdx.x;
+    const int b = i < n ? (keys[i] >> 24) * NB + bucket_of(keys[i] & 0xffffff) : -1;
+    warp_hist_add(hist, b);
+  }
 }
 
 __global__ void k_stage_hist(const Rec* stage, int64_t cnt, int32_t* hist) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt;
-       i += (int64_t)gridDim.x * blockDim.x)
-    if (stage[i].nv > 0) atomicAdd(&hist[bucket_of(stage[i].bound)], 1);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x; i0 < cnt; i0 += stride) {
+    const int64_t i = i0 + threadIdx.x;
+    const int b = (i < cnt && stage[i].nv > 0) ? bucket_of(stage[i].bound) : -1;
+    warp_hist_add(hist, b);
+  }
 }
 
 // Are ranks a != b adjacent?  (the out-row of the lower rank holds the higher one)

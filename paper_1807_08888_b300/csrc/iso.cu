@@ -797,7 +797,7 @@ bool prepare_query(const nuri_query& in, int32_t k, const std::vector<int32_t>& 
 int64_t iso_query_bytes(const nuri_graph* G, int32_t k) {
   const int64_t seeds = std::max<int64_t>(G->d.n, 1);
   const int64_t chunks = seeds + G->d.nnz / kSeedChunk;  // seeds split into first-level chunks
-  const int64_t cap = std::max<int64_t>(16384, (int64_t)k * 64);
+  const int64_t cap = std::max<int64_t>(65536, (int64_t)k * 256);  // the edge ranking's
   return seeds * (2 * 8 + 2 * 8 + 16) + chunks * (4 * 8 + 16) + (int64_t)NBINS * 4 +
          (int64_t)sizeof(IsoState) +
          (int64_t)sizeof(IsoQuery) +
@@ -920,7 +920,9 @@ void topk_iso_batch(nuri_graph* G, int32_t nqueries, const nuri_query* qs, const
   std::vector<int64_t> cap(nqueries), rbase(nqueries + 1);
   // result rows per query (40 B each): room for the rows recorded while tau is still low, so
   // that an overflow (which re-runs the batch) stays rare
-  for (int i = 0; i < nqueries; ++i) cap[i] = std::max<int64_t>(16384, (int64_t)ks[i] * 64);
+  // (ranked by edge weight: four times that -- its looser bounds keep tau lower longer)
+  for (int i = 0; i < nqueries; ++i)
+    cap[i] = std::max<int64_t>(edge ? 65536 : 16384, (int64_t)ks[i] * (edge ? 256 : 64));
   if (const char* e = getenv("NURI_RESULT_CAP"))
     for (int i = 0; i < nqueries; ++i) cap[i] = std::max<int64_t>(1, atoll(e));
   std::vector<char> active(nqueries, 1);
