@@ -1861,12 +1861,16 @@ __device__ __forceinline__ bool adjacent_rank(const DevGraph& g, int32_t a, int3
 // of largest graph degree, then keeping the candidates adjacent to it) and publishes subset_tau of its size.  The cliques themselves
 // are not recorded (the search finds them again); only the lower bound on the k-th best is
 // used, so the answer is unchanged.  buf: max_out entries per warp.
-__global__ void k_greedy_tau(DevGraph g, const int32_t* __restrict__ seeds, int64_t nseeds,
-                             int32_t k, int32_t* __restrict__ buf, int32_t* __restrict__ tau) {
+__global__ void __launch_bounds__(256)
+    k_greedy_tau(DevGraph g, const int32_t* __restrict__ seeds, int64_t nseeds, int32_t k,
+                 int32_t* __restrict__ buf, int32_t* __restrict__ tau) {
   const int lane = threadIdx.x & 31;
   const unsigned FULL = 0xffffffffu;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  __shared__ int32_t sGP[8][64];              // narrow seeds: the candidates (8 warps a block)
+  __shared__ unsigned long long sGRow[8][64];  // and their adjacency rows
+  const int wl = threadIdx.x >> 5;
   int32_t* P = buf + warp * (int64_t)g.max_out;
   for (int64_t i = warp; i < nseeds; i += nwarps) {
     const int32_t v = seeds[i];
@@ -1877,14 +1881,42 @@ __global__ void k_greedy_tau(DevGraph g, const int32_t* __restrict__ seeds, int6
     int c = 1;
     if (p <= 64) {
       // narrow: candidates ordered once by (neighbours among the candidates, graph degree,
-      // -rank); a 64-bit mask keeps the ones adjacent to every candidate added so far
+      // -rank); a 64-bit mask keeps the ones adjacent to every candidate added so far.  The
+      // candidates' adjacency is built once as 64-bit rows in shared memory (each candidate's
+      // out-row scanned by the warp, its entries located in P by binary search)
+      int32_t* sp = sGP[wl];
+      unsigned long long* rows = sGRow[wl];
+      for (int t = lane; t < p; t += 32) sp[t] = P[t];
+      for (int t = lane; t < 64; t += 32) rows[t] = 0ull;
+      __syncwarp();
+      const int32_t plast = sp[p - 1];
+      for (int a = 0; a < p; ++a) {
+        const int64_t rb = g.ooff[sp[a]], re = g.ooff[sp[a] + 1];
+        for (int64_t b0 = rb; b0 < re; b0 += 32) {
+          const int64_t t = b0 + lane;
+          const int32_t y = t < re ? __ldg(g.oout + t) : INT32_MAX;
+          if (y <= plast) {
+            int lo = a + 1, hi = p;  // out-neighbours rank above sp[a]
+            while (lo < hi) {
+              const int mid = (lo + hi) >> 1;
+              if (sp[mid] < y) lo = mid + 1;
+              else hi = mid;
+            }
+            if (lo < p && sp[lo] == y) {
+              atomicOr(&rows[a], 1ull << lo);
+              atomicOr(&rows[lo], 1ull << a);
+            }
+          }
+          if (__all_sync(FULL, y > plast)) break;  // rows are sorted
+        }
+      }
+      __syncwarp();
       long long key[2] = {-1, -1};
       for (int h = 0; h < 2; ++h) {
         const int t = lane + 32 * h;
         if (t >= p) continue;
-        const int32_t x = P[t];
-        int inner = 0;
-        for (int u = 0; u < p; ++u) inner += (u != t && adjacent_rank(g, x, P[u])) ? 1 : 0;
+        const int32_t x = sp[t];
+        const int inner = __popcll(rows[t]);
         const int32_t d = min(__ldg(g.deg + __ldg(g.vert_of + x)), 0xFFFFF);
         key[h] = ((long long)inner << 40) | ((long long)d << 20) |
                  (long long)(0xFFFFF - (x & 0xFFFFF));
@@ -1909,16 +1941,9 @@ __global__ void k_greedy_tau(DevGraph g, const int32_t* __restrict__ seeds, int6
           }
         }
         ++c;
-        const int32_t u = P[bt];
-        alive &= ~(1ull << bt);
-        bool keep[2] = {false, false};
-        for (int h = 0; h < 2; ++h) {
-          const int t = lane + 32 * h;
-          if ((alive >> t) & 1ull) keep[h] = adjacent_rank(g, P[t], u);
-        }
-        alive = (unsigned long long)__ballot_sync(FULL, keep[0]) |
-                ((unsigned long long)__ballot_sync(FULL, keep[1]) << 32);
+        alive &= rows[bt];  // the candidates adjacent to the one added (not itself)
       }
+      __syncwarp();  // the rows are rebuilt for the next seed
       p = 0;
     }
     while (p > 0) {
