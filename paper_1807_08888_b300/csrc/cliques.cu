@@ -462,6 +462,8 @@ __device__ __forceinline__ void and_live(unsigned long long* out, const unsigned
 constexpr int kSliceNodes = 1 << 14;  // nodes a lane searches before it sheds work
 constexpr int kShed = 8;              // levels shed at a time
 constexpr int kFullHandOff = 64;      // pending levels a lane hands on in one go
+constexpr int kTieDefer = 8;          // vertices a tie node must need to be put back
+constexpr int64_t kTieQueue = 1 << 18;  // tie nodes put back at most (per chunk of records)
 // Device memory bounds of one query's buffers (they make the server's admission estimate an
 // upper bound): records handed to the dense tiers or sent back per round, and the dense store
 constexpr int64_t kRoundRecs = 1 << 16;
@@ -471,7 +473,8 @@ constexpr int64_t kStoreBytes = 256ll << 20;
 struct WTask {
   int32_t slot;
   int16_t depth;  // depth + 1 candidates are picked below the record
-  int16_t cont;   // 1: the node was visited already; only its branching remains
+  int16_t cont;   // 1: the node was visited already; only its branching remains;
+                  // 2: as 1, a tie node put back once (searched when taken)
   unsigned long long C[KWIDE];            // the picked candidates (a set: any depth)
   unsigned long long P[KWIDE], X[KWIDE];  // X only in maximal mode
 };
@@ -515,6 +518,10 @@ struct WideStore {
   uint16_t* byid;
   int32_t* rid;
   const int32_t* lexL;
+  // tie nodes put back until the task queue runs dry (null: searched where met)
+  WTask* q_tie;
+  unsigned long long* tie_count;
+  int64_t tie_cap;
 };
 
 // Does every clique of size tau below the node rank after the list lexL?  The node's
@@ -573,6 +580,95 @@ __device__ bool lex_list_after(const WideStore& ws, int slot, int nv, const uint
   return false;
 }
 
+// Search below a tie node: no clique below the node exceeds T = tau (its colour bound equals
+// T), so the cliques of size T that can still rank in the top k are the smallest ones by
+// sorted id list.  Adding one vertex set S to the fixed clique of the node keeps the order of
+// the S parts, so S is built in ascending id order: level l (l vertices chosen) tries its
+// candidates by increasing id, the child of candidate c keeps the untried candidates (all of
+// larger id) adjacent to c, and a level ends once a colouring shows that its untried
+// candidates cannot complete a clique of size T.  Cliques come out in increasing order; after
+// k of them every later clique here has k results before it, and the search stops (all-cliques
+// ranking, ties cut at k).  Levels use lev[0 .. need), cursor positions cur[0 .. need).
+template <int W>
+__device__ void tie_search(const Ctx& cx, const WideStore& ws, int slot, int depth,
+                           uint16_t* pick, const unsigned long long* P0, int T,
+                           unsigned long long (*lev)[W], uint16_t* cur, int32_t& t_cache,
+                           unsigned long long& my_exp, unsigned long long& my_words,
+                           unsigned long long& my_lex, bool& out_of_time) {
+  constexpr int BMW = 64 * W;
+  const unsigned long long* rows = ws.rows + (int64_t)slot * BMW * W;
+  const int32_t* vmap = ws.vmap + (int64_t)slot * BMW;
+  const int32_t* recV = ws.recV + (int64_t)slot * MAXD;
+  const uint16_t* byid = ws.byid + (int64_t)slot * BMW;
+  const int nv = ws.recN[slot];
+  const int p = ws.recP[slot];
+  const int wa = (p + 63) >> 6;
+  const int need = T - (nv + depth + 1);
+  int emitted = 0;
+#pragma unroll
+  for (int q = 0; q < W; ++q) lev[0][q] = q < wa ? P0[q] : 0ull;
+  cur[0] = 0;
+  int l = 0;
+  while (l >= 0) {
+    ++my_exp;
+    if ((my_exp & 31) == 0) {
+      t_cache = ld_volatile(&cx.st->tau);
+      if ((my_exp & 1023) == 0 && past_deadline(cx)) {
+        atomicOr(&cx.st->err, 4);
+        out_of_time = true;
+      }
+    }
+    if (out_of_time || t_cache > T) return;  // every clique left here is below the threshold
+    // the level's bound: its untried candidates must hold need - l more colours
+    unsigned long long R[W];
+#pragma unroll
+    for (int q = 0; q < W; ++q) R[q] = lev[l][q];
+    for (int c = 1; c < need - l && any<W>(R, wa); ++c) {
+      unsigned long long cls[W];
+#pragma unroll
+      for (int q = 0; q < W; ++q) cls[q] = R[q];
+      colour_class<W>(cls, R, rows, wa, my_words);
+    }
+    if (!any<W>(R, wa)) {
+      --l;
+      continue;
+    }
+    // the untried candidate of smallest id
+    int c = -1;
+    while (cur[l] < p) {
+      const int a = byid[cur[l]++];
+      unsigned long long w = 0;
+#pragma unroll
+      for (int q = 0; q < W; ++q)
+        if (q == (a >> 6)) w = lev[l][q];
+      if ((w >> (a & 63)) & 1ull) {
+        c = a;
+        break;
+      }
+    }
+    if (c < 0) {
+      --l;
+      continue;
+    }
+    clear_bit<W>(lev[l], c);
+    pick[depth + 1 + l] = (uint16_t)c;
+    if (l + 1 == need) {  // a clique of size T
+      int32_t pr[MAXD];
+      for (int q = 0; q <= depth + 1 + l; ++q) pr[q] = vmap[pick[q]];
+      add_result(cx, recV, nv, depth + 2 + l, pr);
+      if (++emitted >= cx.k) {
+        ++my_lex;  // the rest of the subtree ranks after these k
+        return;
+      }
+      continue;
+    }
+    and_live<W>(lev[l + 1], lev[l], rows + c * W, wa);
+    my_words += wa;
+    cur[l + 1] = cur[l];  // the child's candidates all have larger ids
+    ++l;
+  }
+}
+
 // Visit the node (record + picks[0..depth], candidates Pn, explored Xn) of a dense record and
 // finish its subtree with colour-ordered branching; if `split` is set and the node has more
 // than split_bits candidates, its viable children become tasks instead (colour order: child
@@ -581,7 +677,7 @@ __device__ bool lex_list_after(const WideStore& ws, int slot, int nv, const uint
 template <int W>
 __device__ void dense_node(const Ctx& cx, const WideStore& ws, int slot, int depth,
                            uint16_t* pick, unsigned long long* Pn, unsigned long long* Xn,
-                           bool split, bool cont, int32_t& t_cache, unsigned long long& my_exp,
+                           bool split, int cont, int32_t& t_cache, unsigned long long& my_exp,
                            unsigned long long& my_pruned, unsigned long long& my_words,
                            unsigned long long& my_lex, bool& limit_hit, bool& out_of_time) {
   constexpr int BMW = 64 * W;
@@ -592,6 +688,45 @@ __device__ void dense_node(const Ctx& cx, const WideStore& ws, int slot, int dep
   const int p = ws.recP[slot];
   const int wa = (p + 63) >> 6;
   const DevGraph& g = cx.g;
+  // Level l keeps rem (candidates not yet branched on), R (high-colour candidates not yet
+  // branched on) and, in maximal mode, X (explored); a tie search below level l uses the levels
+  // above it.
+  unsigned long long stkP[MAXD][W];
+  unsigned long long stkR[MAXD][W];
+  unsigned long long stkX[MAXD][W];
+  uint16_t tcur[MAXD];
+  const int base_depth = depth;
+
+  // Tie nodes (colour bound equal to tau) of a near-complete candidate set (the clique must
+  // take at least half of the candidates) are searched in id order (tie_search).  One that
+  // needs kTieDefer or more vertices is first put back as a task (cont = 2) in the tie queue,
+  // which runs once the task queue is empty: by then the other searches may have raised tau
+  // past it, and it is dropped unsearched.  A task put back once, or a node that finds no room
+  // in the tie queue, is searched at once.
+  const bool tie_ok = ws.cid != nullptr && !cx.maximal && !cx.no_prune;
+  auto tie_node = [&](int d, const unsigned long long* P_, int size) -> bool {
+    const int need = t_cache - size;
+    if (!tie_ok || t_cache == INT32_MIN || t_cache > MAXD || need < 1 || d + need >= MAXD ||
+        2 * need < popc<W>(P_, wa))
+      return false;
+    if (split && ws.q_tie && !(cont == 2 && d == base_depth) && need >= kTieDefer &&
+        (int64_t)ld_volatile(ws.tie_count) < ws.tie_cap) {
+      const unsigned long long b = atomicAdd(ws.tie_count, 1ull);
+      if ((int64_t)b < ws.tie_cap) {
+        WTask* t = ws.q_tie + b;
+        t->slot = slot;
+        t->depth = (int16_t)d;
+        t->cont = 2;
+        write_picks(t, pick, d);
+#pragma unroll
+        for (int q = 0; q < KWIDE; ++q) t->P[q] = q < wa ? P_[q] : 0ull;
+        return true;
+      }
+    }
+    tie_search<W>(cx, ws, slot, d, pick, P_, t_cache, stkR + d + 1, tcur + d + 1, t_cache,
+                  my_exp, my_words, my_lex, out_of_time);
+    return true;
+  };
 
   auto visit_node = [&](int d, const unsigned long long* P_, const unsigned long long* X_) {
     int size = nv + d + 1;
@@ -659,10 +794,12 @@ __device__ void dense_node(const Ctx& cx, const WideStore& ws, int slot, int dep
         }
       }
     };
-    int r = 0;
+    int r = 0, colours = 0;
     walk([&](int, int c, const unsigned long long*) {
       if (c >= cmin) ++r;
+      colours = c;
     });
+    if (r > 0 && size + colours == t_cache && tie_node(depth, Pn, size)) return;
     my_pruned += (unsigned long long)(popc<W>(Pn, wa) - r);
     if (r == 0) return;
     const unsigned long long base = atomicAdd(ws.q_count, (unsigned long long)r);
@@ -694,16 +831,11 @@ __device__ void dense_node(const Ctx& cx, const WideStore& ws, int slot, int dep
       ws.q_out[q].slot = -1;
   }
   // ---- finish the subtree here: colour once per node, branch over its high-colour set ----
-  // Level l keeps rem (candidates not yet branched on), R (high-colour candidates not yet
-  // branched on) and, in maximal mode, X (explored).  A node's R is what is left of its
-  // candidates after greedy colour classes 1 .. tau - |node| - 1 (those that cannot lift a
-  // clique to tau) are taken out; its children come from R, highest index first, child u
-  // having the candidates (rem - u) & N(u), so each clique below the node is reached once,
-  // through the first of its vertices to be branched on.  The colouring is done once per node.
-  unsigned long long stkP[MAXD][W];
-  unsigned long long stkR[MAXD][W];
-  unsigned long long stkX[MAXD][W];
-  const int base_depth = depth;
+  // A node's R is what is left of its candidates after greedy colour classes
+  // 1 .. tau - |node| - 1 (those that cannot lift a clique to tau) are taken out; its children
+  // come from R, highest index first, child u having the candidates (rem - u) & N(u), so each
+  // clique below the node is reached once, through the first of its vertices to be branched
+  // on.  The colouring is done once per node.
   int local = 0;      // nodes entered by this call
   bool fresh = true;  // the node at `depth` (candidates Pn) has not been coloured yet
   // lowc[d]: the clique at depth d holds a vertex with id <= lex_first (tie-aware pruning)
@@ -845,6 +977,17 @@ __device__ void dense_node(const Ctx& cx, const WideStore& ws, int slot, int dep
           }
         }
       }
+      // a tie node (one more colour class empties R): searched in id order, or put back
+      if (level_ok && tie_ok && size < t_cache) {
+        unsigned long long cls[W], R2[W];
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+          cls[q] = R[q];
+          R2[q] = R[q];
+        }
+        colour_class<W>(cls, R2, rows, wa, my_words);
+        if (!any<W>(R2, wa) && tie_node(depth, Pn, size)) level_ok = false;
+      }
       if (level_ok) {
         // the stack keeps only the record's live words (q < wa); reads mask the rest
 #pragma unroll
@@ -930,7 +1073,7 @@ __global__ void __launch_bounds__(128, 6) k_clique_tasks(Ctx cx, WideStore ws,
       Xn[q] = cx.maximal ? T.X[q] : 0ull;
     }
     t_cache = ld_volatile(&cx.st->tau);
-    dense_node<W>(cx, ws, T.slot, T.depth, pick, Pn, Xn, true, T.cont != 0, t_cache, my_exp,
+    dense_node<W>(cx, ws, T.slot, T.depth, pick, Pn, Xn, true, T.cont, t_cache, my_exp,
                   my_pruned, my_words, my_lex, limit_hit, out_of_time);
   }
   if (limit_hit) atomicOr(&cx.st->err, 1);
@@ -961,6 +1104,10 @@ __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
   __shared__ uint16_t sPerm[NW][BMW], sInv[NW][BMW];
   __shared__ int32_t sTot[NW], sNext[NW];
   __shared__ unsigned long long sAlive[NW][W];     // core filter: candidates kept
+  // wide records (512 < |P| <= 1024, narrow instantiation only): degrees and colouring order
+  constexpr int NWC = W == 1 ? NW : 1;
+  constexpr int CBR = W == 1 ? CB_ROWS : 1;
+  __shared__ uint16_t sCbDeg[NWC][CBR], sCbRem[NWC][CBR];
   extern __shared__ unsigned long long dynrows[];  // NW * BMW * W words: adjacency rows of P
 
   const int lane = threadIdx.x & 31;
@@ -1129,34 +1276,78 @@ __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
         }
       }
       __syncwarp();
+      // greedy colouring of P with the candidates in order of degree (highest first: the
+      // initial order of colour-ordered clique search, which tightens the bound), one colour
+      // class at a time, warp-cooperative: the warp scans the uncoloured candidates 32 at a
+      // time, the first one not adjacent to the class joins it and the others are re-tested
+      // against it.  Candidates with fewer than need - 1 neighbours in P cannot be in a clique
+      // reaching tau and are left out.
       int drop = 0;
-      if (lane == 0) {
-        unsigned long long left[CB_W], cls[CB_W];
-        for (int q = 0; q < CB_W; ++q)
-          left[q] = q < cw ? ((q == cw - 1 && (p & 63)) ? ((1ull << (p & 63)) - 1) : ~0ull) : 0ull;
+      if constexpr (W == 1) {
         const int need = tau - nv;  // colours the record needs to reach tau
-        int colours = 0;
-        bool rest = true;
-        while (rest && colours < need) {
-          ++colours;
-          for (int q = 0; q < CB_W; ++q) cls[q] = left[q];
-          for (int q = 0; q < cw; ++q)
-            while (cls[q]) {
-              const int b = __ffsll((long long)cls[q]) - 1;
-              const unsigned long long bit = 1ull << b;
-              cls[q] &= ~bit;
-              left[q] &= ~bit;
-              const unsigned long long* row = cb + (int64_t)(q * 64 + b) * CB_W;
-              for (int r = q; r < cw; ++r) cls[r] &= ~row[r];
-            }
-          unsigned long long a = 0;
-          for (int q = 0; q < cw; ++q) a |= left[q];
-          rest = a != 0;
+        uint16_t* deg = sCbDeg[w];
+        uint16_t* rem = sCbRem[w];  // uncoloured candidates, by degree
+        int alive = 0;
+        for (int i = lane; i < p; i += 32) {
+          int d = 0;
+          for (int q = 0; q < cw; ++q) d += __popcll(cb[(int64_t)i * CB_W + q]);
+          deg[i] = (uint16_t)d;
+          alive += d >= need - 1 ? 1 : 0;
         }
-        drop = (!rest && colours < need) ? 1 : 0;  // |V| + colours < tau
-        if (drop) ++my_pruned;
+        for (int o = 16; o; o >>= 1) alive += __shfl_xor_sync(FULL, alive, o);
+        __syncwarp();
+        if (alive < need) {
+          drop = 1;
+        } else {
+          for (int i = lane; i < p; i += 32) {
+            const int di = deg[i];
+            if (di < need - 1) continue;
+            int r = 0;
+            for (int j = 0; j < p; ++j) {
+              const int dj = deg[j];
+              r += (dj >= need - 1 && (dj > di || (dj == di && j < i))) ? 1 : 0;
+            }
+            rem[r] = (uint16_t)i;
+          }
+          __syncwarp();
+          int nrem = alive, colours = 0;
+          while (nrem > 0 && colours < need) {
+            ++colours;
+            unsigned long long forb = 0ull;  // lane q < cw: word q of the class's neighbours
+            int out = 0;
+            for (int base = 0; base < nrem; base += 32) {
+              const int t = base + lane;
+              const int v = t < nrem ? (int)rem[t] : 0;
+              const unsigned long long fw = __shfl_sync(FULL, forb, (v >> 6) & 31);
+              bool cand = t < nrem && !((fw >> (v & 63)) & 1ull);
+              bool joined = false;
+              unsigned m = __ballot_sync(FULL, cand);
+              while (m) {
+                const int src = __ffs(m) - 1;
+                const int u = __shfl_sync(FULL, v, src);
+                const unsigned long long* row = cb + (int64_t)u * CB_W;
+                if (lane < cw) forb |= row[lane];
+                if (lane == src) {
+                  cand = false;
+                  joined = true;
+                } else if (cand) {
+                  cand = !((row[v >> 6] >> (v & 63)) & 1ull);
+                }
+                m = __ballot_sync(FULL, cand);
+              }
+              const bool stay = t < nrem && !joined;
+              const unsigned sm = __ballot_sync(FULL, stay);
+              __syncwarp();  // every lane holds its entry before the compaction writes
+              if (stay) rem[out + __popc(sm & ((1u << lane) - 1))] = (uint16_t)v;
+              out += __popc(sm);
+              __syncwarp();
+            }
+            nrem = out;
+          }
+          drop = (nrem == 0 && colours < need) ? 1 : 0;  // |V| + colours < tau
+        }
+        if (drop && lane == 0) ++my_pruned;
       }
-      drop = __shfl_sync(FULL, drop, 0);
       if (drop) continue;
     }
     // a record that must be split reserves its children's staging slots first; if the
@@ -1422,7 +1613,7 @@ __global__ void __launch_bounds__(KCfg<W>::WARPS * 32)
             uint16_t pk[MAXD + 1];
             pk[0] = (uint16_t)v0;
             unsigned long long words_here = 0, lex_here = 0;  // counted for the task kernel
-            dense_node<W>(cx, ws, slot, 0, pk, Pi, Xi, false, false, t_cache, my_exp,
+            dense_node<W>(cx, ws, slot, 0, pk, Pi, Xi, false, 0, t_cache, my_exp,
                           my_pruned, words_here, lex_here, limit_hit, out_of_time);
           }
         }
@@ -2182,8 +2373,9 @@ struct DenseBufs {
   DBuf<unsigned long long> rows2, rows4, rows8;
   DBuf<int32_t> vmap2, vmap4, vmap8, recV2, recV4, recV8, recN2, recN4, recN8, recP2, recP4,
       recP8;
-  DBuf<unsigned long long> counters;  // [0] slots, [1] queue count, [2] next task
+  DBuf<unsigned long long> counters;  // [0] slots, [1] queue count, [2] next task, [3] ties
   DBuf<WTask> qa, qb;                 // task queues (wave input and output), grown on demand
+  DBuf<WTask> qt;                     // tie nodes put back (all-cliques ranking)
   DBuf<unsigned long long> low2, low4, low8;  // tie-aware pruning masks per slot
   DBuf<int32_t> reclow2, reclow4, reclow8;
   DBuf<int32_t> lexbuf;                      // smallest id of each size-tau result
@@ -2244,7 +2436,8 @@ WideStore make_store(DenseBufs& B, int W, int64_t nrec, cudaStream_t s) {
       rid.alloc(cap * MAXD, s);
     }
   }
-  if (!B.counters.p) B.counters.alloc(3, s);
+  if (!B.counters.p) B.counters.alloc(4, s);
+  if (B.lex_allowed && !B.qt.p) B.qt.alloc(kTieQueue, s);
   if (B.qmax == 0) {
     B.qmax = task_queue_max();
     if (const char* e = getenv("NURI_TASK_SPLIT")) B.split_bits = std::max(1, atoi(e));
@@ -2277,6 +2470,9 @@ WideStore make_store(DenseBufs& B, int W, int64_t nrec, cudaStream_t s) {
   ws.byid = B.lex_allowed ? byid.p : nullptr;
   ws.rid = B.lex_allowed ? rid.p : nullptr;
   ws.lexL = nullptr;
+  ws.q_tie = B.lex_allowed ? B.qt.p : nullptr;
+  ws.tie_count = B.counters.p + 3;
+  ws.tie_cap = kTieQueue;
   return ws;
 }
 
@@ -2571,7 +2767,7 @@ int64_t run_dense(Ctx cx, const Rec* recs, int64_t nrec, int grid, size_t dyn, D
   for (int64_t c0 = 0; c0 < nrec; c0 += chunk) {
     const int64_t cn = std::min<int64_t>(chunk, nrec - c0);
     WideStore ws = make_store(B, W, cn, s);
-    NURI_CUDA(cudaMemsetAsync(B.counters.p, 0, 3 * sizeof(unsigned long long), s));
+    NURI_CUDA(cudaMemsetAsync(B.counters.p, 0, 4 * sizeof(unsigned long long), s));
     NURI_CUDA(cudaMemsetAsync(&cx.st->work_next, 0, sizeof(int64_t), s));
     NURI_CUDA(cudaEventRecord(tt.c, s));
     k_clique_expand<W><<<grid, KCfg<W>::WARPS * 32, dyn, s>>>(cx, recs + c0, nullptr, cn, ws);
@@ -2600,8 +2796,18 @@ int64_t run_dense(Ctx cx, const Rec* recs, int64_t nrec, int grid, size_t dyn, D
         timed = false;
       }
       int64_t n = std::min<int64_t>((int64_t)cnt, B.qcap);
+      // the task queue is dry: one wave over the tie nodes put back (each is searched or, past
+      // the threshold now, dropped; none is put back again)
+      bool tie_wave = false;
+      if (n == 0 && ws.q_tie) {
+        unsigned long long nt = 0;
+        NURI_CUDA(cudaMemcpyAsync(&nt, B.counters.p + 3, 8, cudaMemcpyDeviceToHost, s));
+        NURI_CUDA(cudaStreamSynchronize(s));
+        n = std::min<int64_t>((int64_t)nt, ws.tie_cap);
+        tie_wave = n > 0;
+      }
       if (n == 0) break;
-      if (n > B.qcap / 8 && B.qcap < B.qmax) {
+      if (!tie_wave && n > B.qcap / 8 && B.qcap < B.qmax) {
         // grow both queues, keeping the pending tasks
         const int64_t cap = std::min<int64_t>(B.qmax, B.qcap * 4);
         DBuf<WTask> na, nb;
@@ -2621,14 +2827,17 @@ int64_t run_dense(Ctx cx, const Rec* recs, int64_t nrec, int grid, size_t dyn, D
       NURI_CUDA(cudaMemcpyAsync(&err, &cx.st->err, 4, cudaMemcpyDeviceToHost, s));
       NURI_CUDA(cudaStreamSynchronize(s));
       if (err & 4) return launched;  // out of time: the caller reports it
-      WTask* in = in_is_a ? B.qa.p : B.qb.p;
+      WTask* in = tie_wave ? B.qt.p : (in_is_a ? B.qa.p : B.qb.p);
       ws.q_out = in_is_a ? B.qb.p : B.qa.p;
-      NURI_CUDA(cudaMemsetAsync(B.counters.p + 1, 0, 2 * sizeof(unsigned long long), s));
+      NURI_CUDA(cudaMemsetAsync(B.counters.p + 1, 0, (tie_wave ? 3 : 2) * sizeof(unsigned long long),
+                                s));
       int tgrid = (int)std::min<int64_t>((n + 127) / 128, (int64_t)resident);
       ws.in_next = B.counters.p + 2;
       ws.in_n = n;
+      WideStore wv = ws;
+      if (tie_wave) wv.q_tie = nullptr;
       NURI_CUDA(cudaEventRecord(tt.a, s));
-      k_clique_tasks<W><<<tgrid, 128, 0, s>>>(cx, ws, in, n, B.counters.p + 2);
+      k_clique_tasks<W><<<tgrid, 128, 0, s>>>(cx, wv, in, n, B.counters.p + 2);
       NURI_CUDA(cudaGetLastError());
       NURI_CUDA(cudaEventRecord(tt.b, s));
       timed = true;
@@ -2736,7 +2945,7 @@ int64_t clique_query_bytes(const nuri_graph* G, int32_t k, uint32_t flags, int64
   b += 2 * res * rec + res * (MAXD * 4 + 4 * 6 + 8);                   // results, merge
   if (g.max_out > 64) {                                                 // dense tiers
     for (int W : {2, 4, KWIDE}) b += slots_per_chunk(W) * slot_bytes(W);
-    b += 2 * task_queue_max() * (int64_t)sizeof(WTask);
+    b += (2 * task_queue_max() + kTieQueue) * (int64_t)sizeof(WTask);
   }
   return b;
 }
