@@ -709,6 +709,14 @@ __device__ void dense_node(const Ctx& cx, const WideStore& ws, int slot, int dep
     if (!tie_ok || t_cache == INT32_MIN || t_cache > MAXD || need < 1 || d + need >= MAXD ||
         2 * need < popc<W>(P_, wa))
       return false;
+    // the node's smallest possible sorted id list ranks after the (k - c_hi)-th known result
+    // of size tau: so does every clique below it
+    if (ws.lexL && ws.lex_tau == t_cache &&
+        lex_list_after<W>(ws, slot, nv, pick, d, P_, need, t_cache)) {
+      ++my_pruned;
+      ++my_lex;
+      return true;
+    }
     if (split && ws.q_tie && !(cont == 2 && d == base_depth) && need >= kTieDefer &&
         (int64_t)ld_volatile(ws.tie_count) < ws.tie_cap) {
       const unsigned long long b = atomicAdd(ws.tie_count, 1ull);
@@ -978,7 +986,7 @@ __device__ void dense_node(const Ctx& cx, const WideStore& ws, int slot, int dep
         }
       }
       // a tie node (one more colour class empties R): searched in id order, or put back
-      if (level_ok && tie_ok && size < t_cache) {
+      if (level_ok && tie_ok && size < t_cache && 2 * (t_cache - size) >= popc<W>(Pn, wa)) {
         unsigned long long cls[W], R2[W];
 #pragma unroll
         for (int q = 0; q < W; ++q) {
