@@ -446,6 +446,14 @@ def profile_case(which, nuri, sptr, repeat=1):
         print(json.dumps({"case": which, "stats": r.stats}))
 
 
+def _pct(v, q):
+    """The q-quantile of the latencies v (nearest rank), None when there are none."""
+    if not v:
+        return None
+    v = sorted(v)
+    return v[min(len(v) - 1, int(q * len(v)))]
+
+
 def serving(args, nuri, torch, sptr):
     """Open-loop serving on the resident R-MAT scale-22 graph: Poisson arrivals of a 50/50 mix
     of top-k clique (k 1..100) and isomorphism (3..8 vertices, k 10..1000) requests at 0.5, 1
@@ -506,6 +514,7 @@ def serving(args, nuri, torch, sptr):
         th = threading.Thread(target=submitter)
         th.start()
         lat, errs, done = [], 0, 0
+        by_kind = {"clique": [], "iso": []}
         pending = set()
         j = 0
         while done < len(reqs):
@@ -526,6 +535,7 @@ def serving(args, nuri, torch, sptr):
                 else:
                     # latency from the scheduled arrival (includes any submission delay)
                     lat.append((time.perf_counter() - start - reqs[q]["t"]) * 1e3)
+                    by_kind[reqs[q]["kind"]].append(lat[-1])
             for q in finished:
                 pending.discard(q)
             done += len(finished)
@@ -541,7 +551,10 @@ def serving(args, nuri, torch, sptr):
             "p50_ms": lat[len(lat) // 2] if lat else None,
             "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))] if lat else None,
             "errors": errs, "iso_batches": st["iso_batches"],
-            "iso_requests": st["iso_batched_requests"]}
+            "iso_requests": st["iso_batched_requests"],
+            "by_kind": {kd: {"count": len(v), "p50_ms": _pct(v, 0.5), "p99_ms": _pct(v, 0.99),
+                             "max_ms": max(v) if v else None}
+                        for kd, v in by_kind.items()}}
     nuri.set_time_budget(0)
     return out
 

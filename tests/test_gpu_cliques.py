@@ -144,7 +144,7 @@ def test_forced_spill_equals_resident(monkeypatch):
     assert b.stats["spilled"] > 0 and b.stats["reloaded"] > 0
 
 
-@pytest.mark.parametrize("split", [5, 16])
+@pytest.mark.parametrize("split", [2, 5, 16])
 def test_split_tier_vs_oracle(monkeypatch, split):
     monkeypatch.setenv("NURI_SPLIT_ABOVE", str(split))
     for g in (synth.rmat(10, 8, seed=1), synth.er_small(120, 0.5, seed=78)):
