@@ -156,7 +156,8 @@ def test_split_tier_vs_oracle(monkeypatch, split):
 
 @pytest.mark.parametrize("n,p", [(150, 0.55), (200, 0.5), (260, 0.45)])
 def test_wide_bitmap_tail_dense_random(n, p):
-    # degeneracy above 64: candidate sets of 65..512 vertices go to the 8-word bitmap tail
+    # degeneracy above 64: candidate sets of 65..256 vertices go to the 2- and 4-word dense
+    # tiers (the 8-word tier, 257..512, is reached by the golden-file tests)
     g = synth.er_small(n, p, seed=77)
     G = load(g)
     assert G.info()["max_out_degree"] > 64
