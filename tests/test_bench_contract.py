@@ -24,3 +24,14 @@ def test_reference_arm_prints_one_json_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["config"]["workload"] == "chunglu1m_top100_cliques"
+
+
+def test_serving_latency_quantiles():
+    """The serving line's p50/p99 (overall and per request kind): nearest rank on the sorted
+    latencies, None for a kind with no requests."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench._pct([], 0.5) is None
+    v = list(range(100, 0, -1))  # 1..100, unsorted
+    assert bench._pct(v, 0.5) == 51 and bench._pct(v, 0.99) == 100
+    assert bench._pct([3.0, 1.0, 2.0], 0.0) == 1.0 and bench._pct([7.0], 0.99) == 7.0
