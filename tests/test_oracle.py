@@ -120,6 +120,36 @@ def test_cliques_closed_form_small_planted():
     assert got == want
 
 
+def test_cliques_closed_form_tied_maxima_matching_complement():
+    """A complete graph minus a perfect matching on 2t of its vertices: every maximal clique
+    takes the universal vertices and one end of each missing edge, so there are 2^t tied
+    maximum cliques.  Ranked by sorted id list, two of them first differ at the missing edge
+    with the smallest lower end among those where they choose differently, and the one taking
+    that lower end ranks first.  With the missing edges ordered by lower end, the r-th
+    maximum clique therefore takes the upper end exactly where the binary digits of r (most
+    significant first) are 1.  Algorithm 1 and BK must produce these rows; the search's tie
+    handling on near-cliques rests on this order."""
+    rng = np.random.default_rng(11)
+    n, t = 26, 6
+    ids = rng.permutation(n)
+    pairs = [tuple(sorted((int(ids[2 * i]), int(ids[2 * i + 1])))) for i in range(t)]
+    universal = sorted(int(x) for x in ids[2 * t:])
+    missing = set(pairs)
+    edges = [(a, b) for a, b in itertools.combinations(range(n), 2) if (a, b) not in missing]
+    g = synth.Graph(n, np.array([e[0] for e in edges], np.int32),
+                    np.array([e[1] for e in edges], np.int32))
+    pairs.sort()  # by lower end
+    want = []
+    for r in range(2 ** t):
+        pick = [pairs[j][(r >> (t - 1 - j)) & 1] for j in range(t)]
+        want.append((n - t, tuple(sorted(universal + pick))))
+    for k in (1, 5, 17, 64):
+        assert [(r[0], r[1]) for r in oracle.topk_cliques(g, k)] == want[:k], k
+        assert [(r[0], r[1]) for r in oracle.bk_cliques(g, k, False)] == want[:k], k
+    # every maximal clique is one of them: the maximal ranking stops at 2^t rows
+    assert [(r[0], r[1]) for r in oracle.bk_cliques(g, 100, True)] == want
+
+
 # ------------------------------------------------------------------------------------------
 # subgraph isomorphism
 # ------------------------------------------------------------------------------------------
